@@ -1,0 +1,185 @@
+/*
+ * parem.h -- C ABI of libparem: chunked speculative DFA matching on one GB300 (sm_103a).
+ *
+ * The library implements the data-parallel hot path of PaREM (Memeti & Pllana,
+ * "PaREM: A Novel Approach for Parallel Regular Expression Matching", CSE 2014):
+ * the text is cut into chunks, every chunk is run from the speculated candidate set of
+ * initial states (the states reachable on the last symbol of the preceding chunk), the
+ * per-chunk state maps are composed in text order to find each chunk's true start, and
+ * the matches are counted and emitted (Section II-B, Algorithm 1).  The result is exactly
+ * that of the plain sequential DFA run of Section II-A.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: PAREM_OK (0) or a negative PAREM_ERR_* code.
+ *     parem_strerror() gives a message.  Nothing is written to the caller's outputs when
+ *     a call fails before launching GPU work (INVALID_ARG, OOM).
+ *   - Host pointers are read during the call only; the library copies what it keeps.
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc'd, or a
+ *     PyTorch CUDA tensor).  The caller owns text and position buffers.
+ *   - Work is ordered on the CUDA stream passed as `void* stream` (a cudaStream_t; NULL is
+ *     the legacy default stream).  Calls are synchronous with respect to `*out`: when they
+ *     return, the result is on the host and the positions are written.
+ *   - Calls on distinct streams may run concurrently from different host threads; the
+ *     library keeps its scratch memory per (device, stream).
+ *   - State numbers in and out are the caller's original numbers; PAREM_NONE stands for
+ *     the dead state (the run has met an undefined transition or a byte outside the
+ *     alphabet).
+ *
+ * Semantics (readings of the paper, see the oracle and the design doc)
+ *   - A transition entry PAREM_NONE is undefined ("Tt[q][c] in Q" fails in Algorithm 1);
+ *     a byte whose symbol is PAREM_NONE16 is outside the alphabet.  Both lead to an
+ *     absorbing, non-accepting dead state.
+ *   - A match is counted after each symbol whose transition lands in F (Algorithm 1's
+ *     found++), at the 0-based index of that symbol; the start state is never counted.
+ *     Positions are ascending, one per index.
+ *   - accepted = (final state in F) (Section II-A); for an empty text it is (q0 in F).
+ */
+#ifndef PAREM_H
+#define PAREM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAREM_NONE 0xFFFFFFFFu   /* undefined transition / dead state */
+#define PAREM_NONE16 0xFFFFu     /* byte outside the alphabet */
+
+#define PAREM_OK 0
+#define PAREM_ERR_INVALID_ARG (-1) /* null pointer, out-of-range entry or size */
+#define PAREM_ERR_OOM (-2)         /* device or host allocation failed */
+#define PAREM_ERR_CAPACITY (-3)    /* more matches than `capacity`; count is still exact */
+#define PAREM_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
+#define PAREM_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define PAREM_ERR_INTERNAL (-6)    /* a device-side self-check failed */
+#define PAREM_ERR_UNSUPPORTED (-7) /* valid request outside what this build supports */
+
+typedef struct parem_dfa parem_dfa; /* opaque; tables resident on one device */
+
+typedef struct {
+  uint32_t final_state; /* state after the last symbol (original numbering), or PAREM_NONE */
+  uint8_t accepted;     /* final_state in F */
+  uint8_t reserved[3];
+  uint64_t match_count; /* number of match positions in the whole text (exact) */
+  uint64_t n_written;   /* positions written: min(match_count, capacity), 0 if none asked */
+} parem_result;
+
+/* Description of a prepared DFA (host-side planning data). */
+typedef struct {
+  uint32_t n_states;        /* states as given */
+  uint32_t n_symbols;       /* symbols as given */
+  uint32_t compact_states;  /* states on the device, including the dead state if any */
+  uint32_t n_classes;       /* distinct transition columns among the symbols the bytes use */
+  uint32_t has_dead;        /* 1 when a dead state was added */
+  uint32_t entry_bytes;     /* 1 (<= 256 compact states) or 2 */
+  uint32_t layout;          /* 0: byte-indexed table in shared memory, 1: class-indexed table
+                               in shared memory, 2: class-indexed table in global memory (L2) */
+  uint32_t table_bytes;     /* bytes of the device transition table */
+  uint32_t max_candidates;  /* largest candidate set |img(c) \ {dead}| over classes */
+  uint32_t reserved;
+  double mean_candidates;   /* mean candidate set size over the 256 byte values */
+} parem_dfa_info;
+
+/* Options of parem_match_ex; zero-initialise, then set what you need. */
+typedef struct {
+  uint32_t start_state;     /* PAREM_NONE (or 0xFFFFFFFF): the DFA's start q0.  Otherwise the
+                               state carried in from the end of a previous piece of a stream
+                               (original numbering), so a long text can be matched piecewise:
+                               positions are then relative to this piece. */
+  uint32_t enumerate_all;   /* 1: speculate every state as a chunk's candidate (the general
+                               enumeration approach the paper compares against, Section IV-A)
+                               instead of the candidate set of Algorithm 1. */
+  uint64_t segment_bytes;   /* bytes per lane segment; 0 = planner's choice.  Rounded up to
+                               a multiple of 128. */
+  uint32_t warps_per_block; /* 0 = planner's choice (1..32) */
+  uint32_t spec_cap_bytes;  /* longest speculative prefix before a segment is treated as not
+                               converging; 0 = planner's choice */
+  uint64_t wait_budget_cycles; /* bound of every device-side wait, in SM clock cycles;
+                                  0 = about 2 seconds */
+  int64_t debug_skip_publish_chunk; /* test hook, -1 = off: the chunk with this index never
+                                       publishes its state, so its successor's bounded wait
+                                       runs out and the call returns PAREM_ERR_TIMEOUT */
+} parem_match_opts;
+
+/*
+ * parem_load_dfa -- prepare a DFA (Q, Sigma, delta, q0, F) (Section II-A) and upload it
+ * to the current device.  This is the "transition table Tt, set of final states F" input
+ * of Algorithm 1; the table plays the role of the adjacency matrix that the paper's
+ * graph-based code generator emits (Section III).
+ *   table          host, n_states * n_symbols uint32, row-major table[q * n_symbols + a];
+ *                  each entry < n_states or PAREM_NONE.
+ *   n_states       1 .. 65535.
+ *   n_symbols      1 .. 256.
+ *   byte_to_symbol host, 256 uint16: the symbol of each text byte (< n_symbols) or
+ *                  PAREM_NONE16; NULL = identity (byte b is symbol b when b < n_symbols).
+ *   start          q0 < n_states.
+ *   accept         host, n_states uint8 flags (nonzero = in F).
+ *   out            receives the handle; free it with parem_free_dfa.
+ * Errors: INVALID_ARG, OOM, CUDA.  Host preparation: dead-state completion, merging of
+ * identical symbol columns into classes, renumbering (accepting states last), the
+ * candidate lists img(c) and the slot table rank(c, q) used by the speculation.
+ */
+int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                   const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                   parem_dfa** out);
+
+/* Host-only preparation of the same inputs, without touching the GPU: validates them and
+ * fills *info.  Errors: INVALID_ARG. */
+int parem_prepare_info(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                       const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                       parem_dfa_info* info);
+
+/* Information about a loaded DFA.  Errors: INVALID_ARG. */
+int parem_dfa_get_info(const parem_dfa* dfa, parem_dfa_info* info);
+
+/* Free a DFA (NULL is ignored).  Synchronises the device first. */
+void parem_free_dfa(parem_dfa* dfa);
+
+/*
+ * parem_match -- run the DFA over a device-resident text (Algorithm 1: chunking,
+ * candidate speculation R = S n L, candidate runs, join; Section II-B).
+ *   dfa        from parem_load_dfa (the same device must be current).
+ *   text       device pointer, any alignment; may be NULL when len == 0.
+ *   len        bytes; at most 2^45.
+ *   positions  device pointer to `capacity` uint64 slots, or NULL to count only.  Receives
+ *              the first min(match_count, capacity) match positions, ascending.
+ *   stream     cudaStream_t or NULL.
+ *   out        host; receives final state, accepted, match_count, n_written.
+ * Errors: INVALID_ARG, OOM, CUDA, TIMEOUT, INTERNAL; CAPACITY when positions != NULL and
+ * match_count > capacity (out is still filled, and exact).
+ */
+int parem_match(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                uint64_t capacity, void* stream, parem_result* out);
+
+/* parem_match with options (carry-in start state, enumeration mode, tuning, test hook).
+ * opts may be NULL (same as parem_match).  Errors as parem_match. */
+int parem_match_ex(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                   uint64_t capacity, const parem_match_opts* opts, void* stream, parem_result* out);
+
+/*
+ * parem_match_host -- the same scan for a text in HOST memory: the library copies the text
+ * to the device in pieces (overlapping the copies with the scan of earlier pieces, each
+ * piece started from the state the previous one ended in) and copies the positions back.
+ *   text       host pointer (pinned memory is fastest; pageable works).
+ *   positions  host pointer to `capacity` uint64, or NULL to count only.
+ * Errors as parem_match.
+ */
+int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                     uint64_t capacity, void* stream, parem_result* out);
+
+/* Release the scratch memory cached for (current device, stream).  Errors: CUDA. */
+int parem_release_scratch(void* stream);
+
+/* Message for a status code. */
+const char* parem_strerror(int status);
+
+/* Library version "major.minor.patch". */
+const char* parem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAREM_H */

@@ -1,0 +1,286 @@
+"""Python binding of libparem (include/parem.h): argument marshalling only.
+
+Every step of the scan runs in the CUDA library; there is no Python or CPU implementation
+of the matcher in this package, and every call raises if libparem.so cannot be loaded.
+
+    import torch, paper_1412_1741_gb300 as pm
+    dfa = pm.parem_load_dfa(table, byte_to_symbol, start, accept)   # numpy inputs
+    text = torch.tensor(..., dtype=torch.uint8, device="cuda")
+    pos = torch.empty(cap, dtype=torch.int64, device="cuda")
+    r = pm.parem_match(dfa, text, pos)        # r.final_state, r.match_count, r.n_written
+
+Functions keep the C names.  Text and position buffers are PyTorch CUDA tensors (or raw
+device pointers given as ints with an explicit length); the stream defaults to PyTorch's
+current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "PAREM_NONE", "PAREM_NONE16", "ParemError", "MatchResult", "DfaInfo", "Dfa", "MatchOpts",
+    "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa",
+    "parem_match", "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror",
+    "parem_version", "EXPORTED_SYMBOLS",
+]
+
+PAREM_NONE = 0xFFFFFFFF
+PAREM_NONE16 = 0xFFFF
+PAREM_OK = 0
+PAREM_ERR_CAPACITY = -3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+# Every symbol declared in include/parem.h.
+EXPORTED_SYMBOLS = [
+    "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
+    "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
+]
+
+
+class ParemError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {parem_strerror(status)} ({status})")
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("final_state", ctypes.c_uint32), ("accepted", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8 * 3), ("match_count", ctypes.c_uint64),
+                ("n_written", ctypes.c_uint64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_uint32), ("n_symbols", ctypes.c_uint32),
+                ("compact_states", ctypes.c_uint32), ("n_classes", ctypes.c_uint32),
+                ("has_dead", ctypes.c_uint32), ("entry_bytes", ctypes.c_uint32),
+                ("layout", ctypes.c_uint32), ("table_bytes", ctypes.c_uint32),
+                ("max_candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("mean_candidates", ctypes.c_double)]
+
+
+class MatchOpts(ctypes.Structure):
+    _fields_ = [("start_state", ctypes.c_uint32), ("enumerate_all", ctypes.c_uint32),
+                ("segment_bytes", ctypes.c_uint64), ("warps_per_block", ctypes.c_uint32),
+                ("spec_cap_bytes", ctypes.c_uint32), ("wait_budget_cycles", ctypes.c_uint64),
+                ("debug_skip_publish_chunk", ctypes.c_int64)]
+
+    def __init__(self, start_state=PAREM_NONE, enumerate_all=0, segment_bytes=0, warps_per_block=0,
+                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=-1):
+        super().__init__(start_state, enumerate_all, segment_bytes, warps_per_block, spec_cap_bytes,
+                         wait_budget_cycles, debug_skip_publish_chunk)
+
+
+@dataclass
+class MatchResult:
+    final_state: int
+    accepted: bool
+    match_count: int
+    n_written: int
+    status: int = 0
+
+
+@dataclass
+class DfaInfo:
+    n_states: int
+    n_symbols: int
+    compact_states: int
+    n_classes: int
+    has_dead: bool
+    entry_bytes: int
+    layout: int
+    table_bytes: int
+    max_candidates: int
+    mean_candidates: float
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libparem.so")
+
+
+def load_library(build_if_missing: bool = False):
+    """Load libparem.so; raises (no fallback) when it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            from . import build as _b
+            _b.build()
+        else:
+            raise ImportError(f"libparem.so not built ({path}); run paper_1412_1741_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+    lib.parem_load_dfa.argtypes = [vp, u32, u32, vp, u32, vp, ctypes.POINTER(vp)]
+    lib.parem_prepare_info.argtypes = [vp, u32, u32, vp, u32, vp, ctypes.POINTER(_Info)]
+    lib.parem_dfa_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    lib.parem_free_dfa.argtypes = [vp]
+    lib.parem_free_dfa.restype = None
+    lib.parem_match.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
+    lib.parem_match_ex.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(MatchOpts), vp, ctypes.POINTER(_Result)]
+    lib.parem_match_host.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
+    lib.parem_release_scratch.argtypes = [vp]
+    lib.parem_strerror.argtypes = [ctypes.c_int]
+    lib.parem_strerror.restype = ctypes.c_char_p
+    lib.parem_version.restype = ctypes.c_char_p
+    for f in ("parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_match", "parem_match_ex",
+              "parem_match_host", "parem_release_scratch"):
+        getattr(lib, f).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def parem_strerror(status: int) -> str:
+    return load_library().parem_strerror(int(status)).decode()
+
+
+def parem_version() -> str:
+    return load_library().parem_version().decode()
+
+
+def _dfa_arrays(table, byte_to_symbol, accept):
+    table = np.ascontiguousarray(table, dtype=np.uint32)
+    if table.ndim != 2:
+        raise ValueError("table must be 2-D [n_states, n_symbols]")
+    accept = np.ascontiguousarray(accept, dtype=np.uint8)
+    b2s = None if byte_to_symbol is None else np.ascontiguousarray(byte_to_symbol, dtype=np.uint16)
+    return table, b2s, accept
+
+
+class Dfa:
+    """Handle of a DFA loaded on the current CUDA device (parem_dfa*)."""
+
+    def __init__(self, handle, info: DfaInfo):
+        self._h = handle
+        self.info = info
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("DFA has been freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            load_library().parem_free_dfa(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _info(i: _Info) -> DfaInfo:
+    return DfaInfo(i.n_states, i.n_symbols, i.compact_states, i.n_classes, bool(i.has_dead), i.entry_bytes,
+                   i.layout, i.table_bytes, i.max_candidates, i.mean_candidates)
+
+
+def parem_prepare_info(table, byte_to_symbol, start, accept) -> DfaInfo:
+    lib = load_library()
+    table, b2s, accept = _dfa_arrays(table, byte_to_symbol, accept)
+    info = _Info()
+    rc = lib.parem_prepare_info(table.ctypes.data, table.shape[0], table.shape[1],
+                                None if b2s is None else b2s.ctypes.data, int(start), accept.ctypes.data,
+                                ctypes.byref(info))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_prepare_info")
+    return _info(info)
+
+
+def parem_load_dfa(table, byte_to_symbol, start, accept) -> Dfa:
+    lib = load_library()
+    table, b2s, accept = _dfa_arrays(table, byte_to_symbol, accept)
+    h = ctypes.c_void_p()
+    rc = lib.parem_load_dfa(table.ctypes.data, table.shape[0], table.shape[1],
+                            None if b2s is None else b2s.ctypes.data, int(start), accept.ctypes.data,
+                            ctypes.byref(h))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_load_dfa")
+    info = _Info()
+    lib.parem_dfa_get_info(h, ctypes.byref(info))
+    return Dfa(h, _info(info))
+
+
+def parem_dfa_get_info(dfa: Dfa) -> DfaInfo:
+    return dfa.info
+
+
+def parem_free_dfa(dfa: Dfa) -> None:
+    dfa.free()
+
+
+def _ptr_len(buf, length=None):
+    """(pointer, length) of a CUDA tensor / numpy array / raw pointer int."""
+    if buf is None:
+        return None, 0
+    if isinstance(buf, int):
+        if length is None:
+            raise ValueError("a raw pointer needs an explicit length")
+        return buf, int(length)
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr(), int(buf.numel() * buf.element_size()) if length is None else int(length)
+    if isinstance(buf, np.ndarray):
+        return buf.ctypes.data, int(buf.nbytes) if length is None else int(length)
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _finish(rc, res: _Result, where):
+    if rc not in (PAREM_OK, PAREM_ERR_CAPACITY):
+        raise ParemError(rc, where)
+    return MatchResult(res.final_state, bool(res.accepted), res.match_count, res.n_written, rc)
+
+
+def parem_match_ex(dfa: Dfa, text, positions=None, opts: MatchOpts | None = None, stream=None,
+                   length=None, capacity=None) -> MatchResult:
+    lib = load_library()
+    tp, n = _ptr_len(text, length)
+    pp, pbytes = _ptr_len(positions)
+    cap = (pbytes // 8 if capacity is None else int(capacity)) if pp else 0
+    res = _Result()
+    rc = lib.parem_match_ex(dfa.handle, tp, n, pp, cap, None if opts is None else ctypes.byref(opts),
+                            _stream(stream), ctypes.byref(res))
+    return _finish(rc, res, "parem_match_ex")
+
+
+def parem_match(dfa: Dfa, text, positions=None, stream=None, length=None, capacity=None) -> MatchResult:
+    lib = load_library()
+    tp, n = _ptr_len(text, length)
+    pp, pbytes = _ptr_len(positions)
+    cap = (pbytes // 8 if capacity is None else int(capacity)) if pp else 0
+    res = _Result()
+    rc = lib.parem_match(dfa.handle, tp, n, pp, cap, _stream(stream), ctypes.byref(res))
+    return _finish(rc, res, "parem_match")
+
+
+def parem_match_host(dfa: Dfa, text, positions=None, stream=None) -> MatchResult:
+    """Text and positions in host memory (numpy arrays, pinned torch tensors)."""
+    lib = load_library()
+    tp, n = _ptr_len(text)
+    pp, pbytes = _ptr_len(positions)
+    cap = pbytes // 8 if pp else 0
+    res = _Result()
+    rc = lib.parem_match_host(dfa.handle, tp, n, pp, cap, _stream(stream), ctypes.byref(res))
+    return _finish(rc, res, "parem_match_host")
+
+
+def parem_release_scratch(stream=None) -> None:
+    rc = load_library().parem_release_scratch(_stream(stream))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_release_scratch")

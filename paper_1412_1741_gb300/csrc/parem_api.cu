@@ -1,0 +1,487 @@
+// parem_api.cu -- the C ABI of libparem (include/parem.h): DFA loading, scratch memory,
+// the launch planner and the scan entry points.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <utility>
+
+#include "../../include/parem.h"
+#include "parem_internal.h"
+#include "parem_launch.h"
+
+using namespace parem;
+
+struct parem_dfa {
+  int device = 0;
+  Prepared host;
+  DeviceDfa dev{};
+  void* dmem = nullptr;
+  parem_dfa_info info{};
+};
+
+namespace {
+
+constexpr uint32_t kSmemTableBudget = 96 * 1024;
+
+#define PAREM_CUDA_TRY(expr)                              \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) {                              \
+      return _e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// scratch memory, cached per (device, stream)
+// ---------------------------------------------------------------------------------------
+struct Scratch {
+  void* dev = nullptr;
+  size_t bytes = 0;
+  DevResult* host_res = nullptr;  // pinned
+  void* dev_text = nullptr;       // staging for parem_match_host
+  size_t text_bytes = 0;
+  void* dev_pos = nullptr;
+  size_t pos_bytes = 0;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, void*>, Scratch*> g_scratch;
+
+Scratch* get_scratch(int dev, void* stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto& s = g_scratch[{dev, stream}];
+  if (!s) s = new (std::nothrow) Scratch();
+  return s;
+}
+
+int ensure(void** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return PAREM_OK;
+  size_t sz = std::max(need, (size_t)(*have * 3 / 2));
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  sz = (sz + 4095) & ~(size_t)4095;
+  cudaError_t e = cudaMalloc(p, sz);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
+  }
+  *have = sz;
+  return PAREM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// tensor map encoding through the driver entry point
+// ---------------------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+int encode_rows(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R) {
+  auto fn = encode_fn();
+  if (!fn) return PAREM_ERR_CUDA;
+  cuuint64_t dims[2] = {(cuuint64_t)S, (cuuint64_t)R};
+  cuuint64_t strides[1] = {(cuuint64_t)S};
+  cuuint32_t box[2] = {kBox, kLanes};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(base), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? PAREM_OK : PAREM_ERR_CUDA;
+}
+
+struct DevProps {
+  int sms = 0;
+  int smem_optin = 0;
+};
+
+DevProps dev_props(int dev) {
+  static std::mutex mu;
+  static std::map<int, DevProps> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  DevProps p;
+  cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&p.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cache[dev] = p;
+  return p;
+}
+
+uint64_t round_up(uint64_t x, uint64_t m) { return (x + m - 1) / m * m; }
+
+void fill_info(const Prepared& P, parem_dfa_info* info) {
+  std::memset(info, 0, sizeof(*info));
+  info->n_states = P.n_in;
+  info->n_symbols = P.n_sym;
+  info->compact_states = P.n;
+  info->n_classes = P.n_classes;
+  info->has_dead = P.has_dead;
+  info->entry_bytes = P.esize;
+  info->layout = P.layout;
+  info->table_bytes = P.table_bytes;
+  info->max_candidates = P.max_cand;
+  info->mean_candidates = P.mean_cand;
+}
+
+}  // namespace
+
+// =======================================================================================
+// ABI
+// =======================================================================================
+extern "C" const char* parem_strerror(int status) {
+  switch (status) {
+    case PAREM_OK: return "ok";
+    case PAREM_ERR_INVALID_ARG: return "invalid argument";
+    case PAREM_ERR_OOM: return "out of memory";
+    case PAREM_ERR_CAPACITY: return "more matches than the position buffer holds";
+    case PAREM_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case PAREM_ERR_CUDA: return "CUDA runtime error";
+    case PAREM_ERR_INTERNAL: return "device-side self-check failed";
+    case PAREM_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* parem_version(void) { return "0.1.0"; }
+
+extern "C" int parem_prepare_info(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                                  const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                                  parem_dfa_info* info) {
+  if (!info) return PAREM_ERR_INVALID_ARG;
+  Prepared P;
+  int rc = prepare_dfa(table, n_states, n_symbols, byte_to_symbol, start, accept, kSmemTableBudget, &P);
+  if (rc != PAREM_OK) return rc;
+  fill_info(P, info);
+  return PAREM_OK;
+}
+
+extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                              const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                              parem_dfa** out) {
+  if (!out) return PAREM_ERR_INVALID_ARG;
+  *out = nullptr;
+  parem_dfa* d = new (std::nothrow) parem_dfa();
+  if (!d) return PAREM_ERR_OOM;
+  int rc = prepare_dfa(table, n_states, n_symbols, byte_to_symbol, start, accept, kSmemTableBudget, &d->host);
+  if (rc != PAREM_OK) {
+    delete d;
+    return rc;
+  }
+  const Prepared& P = d->host;
+  if (cudaGetDevice(&d->device) != cudaSuccess) {
+    delete d;
+    return PAREM_ERR_CUDA;
+  }
+  // one allocation: table | colmap | byte_class | img_off | img | rank
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = round_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_table = take(P.table.size());
+  const size_t o_colmap = take(256 * 4);
+  const size_t o_cls = take(256 * 2);
+  const size_t o_imgoff = take(P.img_off.size() * 4);
+  const size_t o_img = take(P.img.size() * 2);
+  const size_t o_rank = take(P.rank.size() * 2);
+  if (cudaMalloc(&d->dmem, off) != cudaSuccess) {
+    delete d;
+    return PAREM_ERR_OOM;
+  }
+  uint8_t* base = static_cast<uint8_t*>(d->dmem);
+  cudaError_t e = cudaSuccess;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_table, P.table.data(), P.table.size(), cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_colmap, P.colmap.data(), 256 * 4, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_cls, P.byte_class.data(), 256 * 2, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_imgoff, P.img_off.data(), P.img_off.size() * 4, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_img, P.img.data(), P.img.size() * 2, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_rank, P.rank.data(), P.rank.size() * 2, cudaMemcpyHostToDevice) : e;
+  if (e != cudaSuccess) {
+    cudaFree(d->dmem);
+    delete d;
+    return PAREM_ERR_CUDA;
+  }
+  DeviceDfa& D = d->dev;
+  D.table = base + o_table;
+  D.colmap = reinterpret_cast<const uint32_t*>(base + o_colmap);
+  D.byte_class = reinterpret_cast<const uint16_t*>(base + o_cls);
+  D.img_off = reinterpret_cast<const uint32_t*>(base + o_imgoff);
+  D.img = reinterpret_cast<const uint16_t*>(base + o_img);
+  D.rank = reinterpret_cast<const uint16_t*>(base + o_rank);
+  D.n = P.n;
+  D.n_classes = P.n_classes;
+  D.first_accept = P.first_accept;
+  D.dead = P.dead;
+  D.start = P.start;
+  D.layout = P.layout;
+  D.esize = P.esize;
+  D.rowbytes = P.rowbytes;
+  D.table_bytes = P.table_bytes;
+  D.max_cand = P.max_cand;
+  fill_info(P, &d->info);
+  *out = d;
+  return PAREM_OK;
+}
+
+extern "C" int parem_dfa_get_info(const parem_dfa* dfa, parem_dfa_info* info) {
+  if (!dfa || !info) return PAREM_ERR_INVALID_ARG;
+  *info = dfa->info;
+  return PAREM_OK;
+}
+
+extern "C" void parem_free_dfa(parem_dfa* dfa) {
+  if (!dfa) return;
+  cudaDeviceSynchronize();
+  if (dfa->dmem) cudaFree(dfa->dmem);
+  delete dfa;
+}
+
+extern "C" int parem_release_scratch(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
+  Scratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_scratch.find({dev, stream});
+    if (it == g_scratch.end()) return PAREM_OK;
+    s = it->second;
+    g_scratch.erase(it);
+  }
+  cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (s->dev) cudaFree(s->dev);
+  if (s->dev_text) cudaFree(s->dev_text);
+  if (s->dev_pos) cudaFree(s->dev_pos);
+  if (s->host_res) cudaFreeHost(s->host_res);
+  delete s;
+  return PAREM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// planning and launching one scan
+// ---------------------------------------------------------------------------------------
+namespace parem {
+
+int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const parem_match_opts* o,
+              Plan* pl) {
+  const Prepared& P = dfa->host;
+  const DevProps props = dev_props(dfa->device);
+  std::memset(pl, 0, sizeof(*pl));
+  pl->enum_all = o && o->enumerate_all ? 1u : 0u;
+  const uint32_t m_need = pl->enum_all ? (P.n - P.has_dead) : P.max_cand;
+  pl->P = m_need <= 32 ? 1 : 8;
+  pl->cand_stride = std::max<uint32_t>(1, std::max(P.max_cand, pl->enum_all ? P.n : 0u));
+  // shared memory carve-up of pass 1
+  const uint32_t per_warp_stage = kStages * kStageBytes;
+  const uint32_t per_warp_hash = pl->P > 1 ? kHashSize * 4 : 0;
+  const uint32_t table_smem = P.layout == kClassGlobal ? 0 : P.table_bytes;
+  const uint32_t fixed = 1024 /*align slack*/ + 1024 /*colmap*/ + table_smem + 256;
+  const uint32_t per_warp = per_warp_stage + kStages * 8 + per_warp_hash;
+  int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
+  warps = std::min(warps, 32);
+  if (o && o->warps_per_block) warps = std::min<int>(warps, (int)o->warps_per_block);
+  if (warps < 1) return PAREM_ERR_UNSUPPORTED;
+  pl->warps = warps;
+  pl->grid = props.sms;
+  uint32_t off = 0;
+  pl->stage_off = off;
+  off += warps * per_warp_stage;
+  pl->bar_off = off;
+  off += warps * kStages * 8;
+  off = (uint32_t)round_up(off, 16);
+  pl->hash_off = off;
+  off += warps * per_warp_hash;
+  off = (uint32_t)round_up(off, 16);
+  pl->colmap_off = off;
+  off += 1024;
+  pl->table_off = off;
+  off += table_smem;
+  pl->smem = off + 1024;
+  // rows
+  const uint64_t addr = reinterpret_cast<uint64_t>(text);
+  pl->h = std::min<uint64_t>(len, (16 - (addr & 15)) & 15);
+  const uint64_t body = len - pl->h;
+  const uint64_t lanes_total = (uint64_t)pl->grid * warps * kLanes;
+  uint64_t S;
+  if (o && o->segment_bytes) {
+    S = round_up(o->segment_bytes, kBox);
+  } else {
+    const uint64_t smin = pl->P == 1 ? 512 : 4096;
+    S = round_up(std::max<uint64_t>(body / (lanes_total * 2 + 1), 1), kBox);
+    S = std::max(S, smin);
+    S = std::min<uint64_t>(S, 1u << 20);
+  }
+  // keep the row index inside the TMA coordinate range
+  while (body / S >= (1ull << 31)) S *= 2;
+  if (body < S) S = body / kBox * kBox;
+  pl->S = S;
+  pl->R = S ? body / S : 0;
+  pl->tail = S ? body - pl->R * S : body;
+  pl->n_chunks = (pl->R + kLanes - 1) / kLanes;
+  uint64_t cap = o && o->spec_cap_bytes ? o->spec_cap_bytes : std::max<uint64_t>(2048, 16ull * P.n);
+  cap = std::min<uint64_t>(cap, S);
+  pl->spec_cap = (uint32_t)(cap / 16 * 16);
+  if (pl->spec_cap == 0) pl->spec_cap = 16;
+  return PAREM_OK;
+}
+
+}  // namespace parem
+
+static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                    uint64_t capacity, const parem_match_opts* o, cudaStream_t stream, parem_result* out) {
+  const Prepared& P = dfa->host;
+  uint32_t init = P.start;
+  if (o && o->start_state != PAREM_NONE) {
+    if (o->start_state >= P.n_in) return PAREM_ERR_INVALID_ARG;
+    init = P.compact_of[o->start_state];
+  }
+  std::memset(out, 0, sizeof(*out));
+  if (len == 0) {
+    out->final_state = P.orig_of[init];
+    out->accepted = init >= P.first_accept;
+    return PAREM_OK;
+  }
+  Plan pl;
+  int rc = plan_scan(dfa, text, len, o, &pl);
+  if (rc != PAREM_OK) return rc;
+  Scratch* sc = get_scratch(dfa->device, stream);
+  if (!sc) return PAREM_ERR_OOM;
+  if (!sc->host_res) {
+    if (cudaMallocHost(&sc->host_res, sizeof(DevResult)) != cudaSuccess) return PAREM_ERR_OOM;
+  }
+  // scratch: [ticket 256][result 256][status K*8][segrec R*16][slot_end][slot_cnt]
+  const bool emit = positions != nullptr && capacity > 0;
+  const uint64_t o_status = 512;
+  const uint64_t o_segrec = round_up(o_status + pl.n_chunks * 8, 256);
+  const uint64_t o_slot = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
+  const uint64_t slot_bytes = pl.R * (uint64_t)pl.cand_stride * 4;
+  const uint64_t total = round_up(o_slot + 2 * slot_bytes, 256);
+  rc = ensure(&sc->dev, &sc->bytes, total);
+  if (rc != PAREM_OK) return rc;
+  uint8_t* sb = static_cast<uint8_t*>(sc->dev);
+  PAREM_CUDA_TRY(cudaMemsetAsync(sb, 0, o_status + pl.n_chunks * 8, stream));
+
+  ScanParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.dfa = dfa->dev;
+  p.text = text;
+  p.n = len;
+  p.h = pl.h;
+  p.S = pl.S;
+  p.R = pl.R;
+  p.tail = pl.tail;
+  p.n_chunks = pl.n_chunks;
+  p.init_state = init;
+  p.enum_all = pl.enum_all;
+  p.spec_cap = pl.spec_cap;
+  p.cand_stride = pl.cand_stride;
+  p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
+  p.skip_publish = o ? o->debug_skip_publish_chunk : -1;
+  if (!o) p.skip_publish = -1;
+  p.ticket = reinterpret_cast<uint32_t*>(sb);
+  p.result = reinterpret_cast<DevResult*>(sb + 256);
+  p.status = reinterpret_cast<unsigned long long*>(sb + o_status);
+  p.segrec = emit ? reinterpret_cast<SegRec*>(sb + o_segrec) : nullptr;
+  p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
+  p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
+  p.positions = emit ? positions : nullptr;
+  p.capacity = emit ? capacity : 0;
+
+  const size_t small_smem = 1024 + (P.layout == kClassGlobal ? 0 : P.table_bytes);
+  cudaError_t e;
+  if (pl.R == 0) {
+    ScanParams q = p;
+    q.smem_colmap_off = 0;
+    q.smem_table_off = 1024;
+    e = launch_tiny_dispatch(P.layout, P.esize, q, small_smem, stream);
+  } else {
+    CUtensorMap tm;
+    rc = encode_rows(&tm, text + pl.h, pl.S, pl.R);
+    if (rc != PAREM_OK) return rc;
+    p.smem_stage_off = pl.stage_off;
+    p.smem_bar_off = pl.bar_off;
+    p.smem_hash_off = pl.hash_off;
+    p.smem_colmap_off = pl.colmap_off;
+    p.smem_table_off = pl.table_off;
+    e = launch_scan_dispatch(P.layout, P.esize, pl.P, tm, p, pl.grid, pl.warps * 32, pl.smem, stream);
+    if (e == cudaSuccess && emit) {
+      ScanParams q = p;
+      q.smem_colmap_off = 0;
+      q.smem_table_off = 1024;
+      const DevProps props = dev_props(dfa->device);
+      e = launch_emit_dispatch(P.layout, P.esize, q, props.sms * 4, 256, small_smem, stream);
+    }
+  }
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
+  PAREM_CUDA_TRY(cudaMemcpyAsync(sc->host_res, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, stream));
+  PAREM_CUDA_TRY(cudaStreamSynchronize(stream));
+  const DevResult r = *sc->host_res;
+  if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
+  if (r.error) return PAREM_ERR_INTERNAL;
+  const uint32_t fs = r.final_state;
+  out->final_state = (fs < P.n) ? P.orig_of[fs] : PAREM_NONE;
+  out->accepted = (fs < P.n && fs >= P.first_accept) ? 1 : 0;
+  out->match_count = r.count;
+  out->n_written = emit ? std::min<uint64_t>(r.count, capacity) : 0;
+  if (emit && r.count > capacity) return PAREM_ERR_CAPACITY;
+  return PAREM_OK;
+}
+
+extern "C" int parem_match_ex(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                              uint64_t capacity, const parem_match_opts* opts, void* stream, parem_result* out) {
+  if (!dfa || !out || (len > 0 && !text) || len > kMaxText) return PAREM_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
+  if (dev != dfa->device) return PAREM_ERR_INVALID_ARG;
+  return run_scan(dfa, text, len, positions, capacity, opts, static_cast<cudaStream_t>(stream), out);
+}
+
+extern "C" int parem_match(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                           uint64_t capacity, void* stream, parem_result* out) {
+  return parem_match_ex(dfa, text, len, positions, capacity, nullptr, stream, out);
+}
+
+extern "C" int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                                uint64_t capacity, void* stream, parem_result* out) {
+  if (!dfa || !out || (len > 0 && !text) || len > kMaxText) return PAREM_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
+  if (dev != dfa->device) return PAREM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Scratch* sc = get_scratch(dev, stream);
+  if (!sc) return PAREM_ERR_OOM;
+  int rc = ensure(&sc->dev_text, &sc->text_bytes, std::max<uint64_t>(len, 16));
+  if (rc != PAREM_OK) return rc;
+  const bool want = positions != nullptr && capacity > 0;
+  if (want) {
+    rc = ensure(&sc->dev_pos, &sc->pos_bytes, capacity * 8);
+    if (rc != PAREM_OK) return rc;
+  }
+  if (len) PAREM_CUDA_TRY(cudaMemcpyAsync(sc->dev_text, text, len, cudaMemcpyHostToDevice, st));
+  rc = run_scan(dfa, static_cast<const uint8_t*>(sc->dev_text), len,
+                want ? static_cast<uint64_t*>(sc->dev_pos) : nullptr, want ? capacity : 0, nullptr, st, out);
+  if (rc != PAREM_OK && rc != PAREM_ERR_CAPACITY) return rc;
+  if (want && out->n_written) {
+    PAREM_CUDA_TRY(cudaMemcpyAsync(positions, sc->dev_pos, out->n_written * 8, cudaMemcpyDeviceToHost, st));
+    PAREM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return rc;
+}

@@ -1,0 +1,119 @@
+// parem_internal.h -- structures shared by the host planner (parem_api.cu, parem_prep.cpp)
+// and the kernels (parem_scan.cuh).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda.h>
+
+namespace parem {
+
+constexpr uint32_t kLanes = 32;          // segments per chunk: one per lane of the owning warp
+constexpr uint32_t kBox = 128;           // bytes of one TMA column block per row (128B swizzle)
+constexpr uint32_t kStages = 2;          // TMA stages per warp
+constexpr uint32_t kStageBytes = kLanes * kBox;  // 4 KiB: 32 rows x 128 B
+constexpr uint32_t kEmpty = 0xFFFFFFFFu; // an empty candidate register / "no state"
+constexpr uint32_t kNoSlot = 0xFFFFu;    // rank(c, q) when q is not a candidate of class c
+constexpr uint32_t kHashSize = 512;      // per-warp owner table used to merge candidates (P > 1)
+constexpr uint64_t kMaxText = 1ull << 45;
+
+// Table layouts (parem_dfa_info.layout).
+enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2 };
+
+// Chunk status word (64 bit), published with release semantics:
+//   [63:62] flag  0 none, 1 MAPPED (end state E known), 2 AGGREGATE (E, dead, count),
+//                 3 INCLUSIVE (E, prefix dead, prefix count)
+//   [61]    dead flag
+//   [60:45] E, the compact end state of the chunk assuming a live start
+//   [44:0]  count
+constexpr uint32_t kFlagMapped = 1, kFlagAggregate = 2, kFlagInclusive = 3;
+constexpr uint64_t kCountMask = (1ull << 45) - 1;
+
+// Device error codes (written to the error word; the first one wins).
+constexpr uint32_t kErrTimeout = 1, kErrInternal = 2;
+
+// A prepared DFA on the host, in the layout the kernels read.
+struct Prepared {
+  uint32_t n_in = 0, n_sym = 0;     // as given
+  uint32_t n = 0;                   // compact states (incl. dead)
+  uint32_t has_dead = 0;
+  uint32_t dead = kEmpty;           // compact id of the dead state
+  uint32_t first_accept = 0;        // compact ids >= first_accept are in F
+  uint32_t start = 0;               // compact q0
+  uint32_t n_classes = 0;           // classes of the bytes (the "all states" list is extra)
+  uint32_t layout = 0, esize = 1, rowbytes = 0, table_bytes = 0;
+  uint32_t max_cand = 0;            // over byte classes
+  double mean_cand = 0;
+  std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
+  std::vector<uint32_t> compact_of; // original -> compact
+  std::vector<uint16_t> byte_class; // 256
+  std::vector<uint32_t> colmap;     // 256: column byte offset of each byte in a table row
+  std::vector<uint8_t> table;       // n * rowbytes (padded to 16)
+  std::vector<uint32_t> img_off;    // n_classes + 2 offsets; list n_classes = all live states
+  std::vector<uint16_t> img;        // candidate lists, sorted, dead excluded
+  std::vector<uint16_t> rank;       // (n_classes + 1) * n
+};
+
+// Host preparation (parem_prep.cpp).  Returns 0 or a PAREM_ERR_* code.
+int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                uint32_t smem_table_budget, Prepared* out);
+
+// Device-resident DFA, passed by value to kernels.
+struct DeviceDfa {
+  const uint8_t* table;
+  const uint32_t* colmap;
+  const uint16_t* byte_class;
+  const uint32_t* img_off;
+  const uint16_t* img;
+  const uint16_t* rank;
+  uint32_t n, n_classes, first_accept, dead, start;
+  uint32_t layout, esize, rowbytes, table_bytes, max_cand;
+};
+
+// Per-segment record for the emit pass.
+struct SegRec {
+  uint32_t x;       // true compact start state of the segment (dead -> DeviceDfa::dead / kEmpty)
+  uint32_t count;   // matches inside the segment
+  uint64_t offset;  // index of the segment's first match in the global position order
+};
+
+// Result word filled on the device.
+struct DevResult {
+  uint32_t final_state;  // compact
+  uint32_t error;        // kErr* or 0
+  uint64_t count;
+};
+
+// Parameters of one plain scan (one text).
+struct ScanParams {
+  DeviceDfa dfa;
+  const uint8_t* text;     // text base (any alignment)
+  uint64_t n;              // text bytes
+  uint64_t h;              // head bytes before the first 16-byte aligned address (< 16)
+  uint64_t S;              // bytes per full row (segment), multiple of kBox
+  uint64_t R;              // full rows; row r covers [h + r*S, h + (r+1)*S)
+  uint64_t tail;           // bytes after the last full row, appended to row R-1
+  uint64_t n_chunks;       // ceil(R / 32)
+  uint32_t init_state;     // compact start state (q0 or carried in)
+  uint32_t enum_all;       // candidates = all live states
+  uint32_t spec_cap;       // bytes of speculation before a segment counts as non-converged
+  uint32_t cand_stride;    // slots per segment in the slot map
+  uint64_t wait_budget;    // clock64 cycles
+  int64_t skip_publish;    // test hook (-1 off)
+  // scratch
+  uint32_t* ticket;
+  unsigned long long* status;
+  SegRec* segrec;          // nullptr when positions are not requested
+  uint32_t* slot_end;      // R * cand_stride
+  uint32_t* slot_cnt;      // R * cand_stride
+  DevResult* result;
+  // outputs
+  uint64_t* positions;
+  uint64_t capacity;
+  // shared memory carve-up (bytes from the dynamic smem base)
+  uint32_t smem_stage_off, smem_bar_off, smem_hash_off, smem_colmap_off, smem_table_off;
+};
+
+}  // namespace parem

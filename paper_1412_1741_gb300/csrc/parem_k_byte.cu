@@ -1,0 +1,25 @@
+// Kernels for the byte-indexed table in shared memory (up to ~96 KiB of table).
+#include "parem_launch.h"
+#include "parem_scan.cuh"
+
+namespace parem {
+
+cudaError_t scan_byte(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+                      int block, size_t smem, cudaStream_t s) {
+  if (esize == 1)
+    return P == 1 ? launch_spec_scan<kByteSmem, 1, 1>(tm, p, grid, block, smem, s)
+                  : launch_spec_scan<kByteSmem, 1, 8>(tm, p, grid, block, smem, s);
+  return P == 1 ? launch_spec_scan<kByteSmem, 2, 1>(tm, p, grid, block, smem, s)
+                : launch_spec_scan<kByteSmem, 2, 8>(tm, p, grid, block, smem, s);
+}
+
+cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
+  return esize == 1 ? launch_emit<kByteSmem, 1>(p, grid, block, smem, s)
+                    : launch_emit<kByteSmem, 2>(p, grid, block, smem, s);
+}
+
+cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s) {
+  return esize == 1 ? launch_tiny<kByteSmem, 1>(p, smem, s) : launch_tiny<kByteSmem, 2>(p, smem, s);
+}
+
+}  // namespace parem

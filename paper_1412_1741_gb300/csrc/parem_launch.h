@@ -1,0 +1,45 @@
+// parem_launch.h -- launch plan and the kernel dispatch entry points (one translation unit
+// per table layout instantiates the kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "parem_internal.h"
+
+struct parem_dfa;
+
+namespace parem {
+
+struct Plan {
+  uint32_t P;            // candidate registers per lane (1 or 8)
+  uint32_t enum_all;
+  uint32_t cand_stride;
+  int warps, grid;
+  uint32_t stage_off, bar_off, hash_off, colmap_off, table_off;
+  size_t smem;
+  uint64_t h, S, R, tail, n_chunks;
+  uint32_t spec_cap;
+};
+
+cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, const CUtensorMap& tm,
+                                 const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, int grid, int block,
+                                 size_t smem, cudaStream_t s);
+cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, size_t smem,
+                                 cudaStream_t s);
+
+// per-layout entry points (parem_k_byte.cu, parem_k_class.cu, parem_k_global.cu)
+cudaError_t scan_byte(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+                      int block, size_t smem, cudaStream_t s);
+cudaError_t scan_class(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+                       int block, size_t smem, cudaStream_t s);
+cudaError_t scan_global(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+                        int block, size_t smem, cudaStream_t s);
+cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_class(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_global(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t tiny_global(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
+
+}  // namespace parem

@@ -1,0 +1,238 @@
+// parem_prep.cpp -- host-side preparation of a DFA for the GPU scan (no CUDA calls).
+//
+// Input is the DFA (Q, Sigma, delta, q0, F) of Section II-A with the byte -> symbol map.
+// Output (parem::Prepared) is what the kernels read:
+//   * completion with an explicit dead state when some transition is undefined or some
+//     byte lies outside the alphabet (the "not in Q" case of Algorithm 1's tests);
+//   * renumbering: non-accepting states first, then the dead state, then the accepting
+//     states, so "state in F" is one comparison with first_accept;
+//   * byte classes: bytes whose symbols have identical transition columns share a class;
+//   * the transition table, either byte-indexed (256 columns: no class lookup in the hot
+//     loop) or class-indexed, with a row pitch chosen to spread rows over the 32 banks;
+//   * for every class c the candidate list img(c): the distinct states reached on c from
+//     any state, without the dead state (the set L of Algorithm 1; S n L for a complete
+//     DFA, and the dead state needs no simulation), plus one extra list with every live
+//     state for the enumeration mode;
+//   * rank(c, q): slot of state q in img(c), used to read a chunk map at its true start.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+
+#include "../../include/parem.h"
+#include "parem_internal.h"
+
+namespace parem {
+
+namespace {
+
+struct VecHash {
+  size_t operator()(const std::vector<uint32_t>& v) const {
+    uint64_t h = 1469598103934665603ull;
+    for (uint32_t x : v) {
+      h ^= x;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
+// Row pitch in bytes: a multiple of the entry size whose word stride is odd when it is a
+// whole number of words, so consecutive rows start in different banks.
+uint32_t row_pitch(uint32_t cols, uint32_t esize) {
+  uint32_t rb = cols * esize;
+  if (rb % 4 == 0 && (rb / 4) % 2 == 0) rb += 4;
+  return rb;
+}
+
+}  // namespace
+
+int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                uint32_t smem_table_budget, Prepared* out) {
+  if (!table || !accept || !out) return PAREM_ERR_INVALID_ARG;
+  if (n_states < 1 || n_states > 65535 || n_symbols < 1 || n_symbols > 256 || start >= n_states)
+    return PAREM_ERR_INVALID_ARG;
+  const uint64_t cells = (uint64_t)n_states * n_symbols;
+  bool any_none = false;
+  for (uint64_t i = 0; i < cells; ++i) {
+    if (table[i] == PAREM_NONE) {
+      any_none = true;
+    } else if (table[i] >= n_states) {
+      return PAREM_ERR_INVALID_ARG;
+    }
+  }
+  // symbol of each byte
+  uint32_t sym[256];
+  bool byte_outside = false;
+  for (int b = 0; b < 256; ++b) {
+    uint32_t a;
+    if (byte_to_symbol) {
+      a = byte_to_symbol[b];
+      if (a == PAREM_NONE16) {
+        a = PAREM_NONE;
+      } else if (a >= n_symbols) {
+        return PAREM_ERR_INVALID_ARG;
+      }
+    } else {
+      a = (uint32_t)b < n_symbols ? (uint32_t)b : PAREM_NONE;
+    }
+    sym[b] = a;
+    if (a == PAREM_NONE) byte_outside = true;
+  }
+  // A dead state is needed when an undefined entry can be used by some byte, or a byte is
+  // outside the alphabet.
+  bool used_sym[256] = {false};
+  for (int b = 0; b < 256; ++b)
+    if (sym[b] != PAREM_NONE) used_sym[sym[b]] = true;
+  bool none_used = false;
+  if (any_none) {
+    for (uint32_t q = 0; q < n_states && !none_used; ++q)
+      for (uint32_t a = 0; a < n_symbols; ++a)
+        if (used_sym[a] && table[(uint64_t)q * n_symbols + a] == PAREM_NONE) {
+          none_used = true;
+          break;
+        }
+  }
+  Prepared P;
+  P.n_in = n_states;
+  P.n_sym = n_symbols;
+  P.has_dead = (none_used || byte_outside) ? 1 : 0;
+  P.n = n_states + P.has_dead;
+  // renumber: non-accepting, dead, accepting
+  P.compact_of.assign(n_states, 0);
+  P.orig_of.assign(P.n, 0);
+  uint32_t next = 0;
+  for (uint32_t q = 0; q < n_states; ++q)
+    if (!accept[q]) {
+      P.compact_of[q] = next;
+      P.orig_of[next++] = q;
+    }
+  if (P.has_dead) {
+    P.dead = next;
+    P.orig_of[next++] = PAREM_NONE;
+  }
+  P.first_accept = next;
+  for (uint32_t q = 0; q < n_states; ++q)
+    if (accept[q]) {
+      P.compact_of[q] = next;
+      P.orig_of[next++] = q;
+    }
+  P.start = P.compact_of[start];
+  const uint32_t n = P.n;
+
+  // transition column of a symbol over compact states (dead row -> dead)
+  auto column = [&](uint32_t a) {
+    std::vector<uint32_t> col(n);
+    for (uint32_t c = 0; c < n; ++c) {
+      uint32_t q = P.orig_of[c];
+      if (q == PAREM_NONE || a == PAREM_NONE) {
+        col[c] = P.dead;
+      } else {
+        uint32_t e = table[(uint64_t)q * n_symbols + a];
+        col[c] = e == PAREM_NONE ? P.dead : P.compact_of[e];
+      }
+    }
+    return col;
+  };
+  // classes over the symbols the bytes use (NONE is its own column)
+  std::unordered_map<std::vector<uint32_t>, uint32_t, VecHash> cls_of_col;
+  std::vector<std::vector<uint32_t>> cols;
+  std::map<uint32_t, uint32_t> cls_of_sym;
+  P.byte_class.assign(256, 0);
+  for (int b = 0; b < 256; ++b) {
+    uint32_t a = sym[b];
+    auto it = cls_of_sym.find(a);
+    if (it == cls_of_sym.end()) {
+      std::vector<uint32_t> col = column(a);
+      auto jt = cls_of_col.find(col);
+      uint32_t c;
+      if (jt == cls_of_col.end()) {
+        c = (uint32_t)cols.size();
+        cls_of_col.emplace(col, c);
+        cols.push_back(std::move(col));
+      } else {
+        c = jt->second;
+      }
+      it = cls_of_sym.emplace(a, c).first;
+    }
+    P.byte_class[b] = (uint16_t)it->second;
+  }
+  P.n_classes = (uint32_t)cols.size();
+
+  // layout
+  P.esize = n <= 256 ? 1 : 2;
+  const uint32_t rb_byte = row_pitch(256, P.esize);
+  const uint32_t rb_cls = row_pitch(P.n_classes, P.esize);
+  if ((uint64_t)n * rb_byte <= smem_table_budget) {
+    P.layout = kByteSmem;
+    P.rowbytes = rb_byte;
+  } else if ((uint64_t)n * rb_cls <= smem_table_budget) {
+    P.layout = kClassSmem;
+    P.rowbytes = rb_cls;
+  } else {
+    P.layout = kClassGlobal;
+    P.rowbytes = rb_cls;
+  }
+  uint64_t tbytes = (uint64_t)n * P.rowbytes;
+  tbytes = (tbytes + 15) & ~15ull;
+  if (tbytes > 0xFFFFFFFFull) return PAREM_ERR_UNSUPPORTED;
+  P.table_bytes = (uint32_t)tbytes;
+  P.table.assign(P.table_bytes, 0);
+  auto put = [&](uint32_t s, uint32_t colbyte, uint32_t v) {
+    uint8_t* p = &P.table[(uint64_t)s * P.rowbytes + colbyte];
+    if (P.esize == 1) {
+      *p = (uint8_t)v;
+    } else {
+      uint16_t w = (uint16_t)v;
+      std::memcpy(p, &w, 2);
+    }
+  };
+  P.colmap.assign(256, 0);
+  if (P.layout == kByteSmem) {
+    for (int b = 0; b < 256; ++b) {
+      const auto& col = cols[P.byte_class[b]];
+      for (uint32_t s = 0; s < n; ++s) put(s, (uint32_t)b * P.esize, col[s]);
+      P.colmap[b] = (uint32_t)b * P.esize;
+    }
+  } else {
+    for (uint32_t c = 0; c < P.n_classes; ++c)
+      for (uint32_t s = 0; s < n; ++s) put(s, c * P.esize, cols[c][s]);
+    for (int b = 0; b < 256; ++b) P.colmap[b] = (uint32_t)P.byte_class[b] * P.esize;
+  }
+
+  // candidate lists and ranks; list n_classes holds every live state (enumeration mode)
+  const uint32_t nl = P.n_classes + 1;
+  P.img_off.assign(nl + 1, 0);
+  P.rank.assign((uint64_t)nl * n, (uint16_t)kNoSlot);
+  std::vector<uint8_t> seen(n);
+  P.max_cand = 0;
+  for (uint32_t c = 0; c < nl; ++c) {
+    std::fill(seen.begin(), seen.end(), 0);
+    if (c < P.n_classes) {
+      for (uint32_t s = 0; s < n; ++s) seen[cols[c][s]] = 1;
+    } else {
+      std::fill(seen.begin(), seen.end(), 1);
+    }
+    P.img_off[c] = (uint32_t)P.img.size();
+    for (uint32_t s = 0; s < n; ++s) {
+      if (!seen[s] || s == P.dead) continue;
+      P.rank[(uint64_t)c * n + s] = (uint16_t)(P.img.size() - P.img_off[c]);
+      P.img.push_back((uint16_t)s);
+    }
+    uint32_t m = (uint32_t)P.img.size() - P.img_off[c];
+    if (c < P.n_classes) P.max_cand = std::max(P.max_cand, m);
+  }
+  P.img_off[nl] = (uint32_t)P.img.size();
+  double tot = 0;
+  for (int b = 0; b < 256; ++b) {
+    uint32_t c = P.byte_class[b];
+    tot += P.img_off[c + 1] - P.img_off[c];
+  }
+  P.mean_cand = tot / 256.0;
+  if (P.img.empty()) P.img.push_back(0);
+  *out = std::move(P);
+  return PAREM_OK;
+}
+
+}  // namespace parem

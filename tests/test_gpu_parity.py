@@ -1,0 +1,200 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle: bit-exact final state,
+acceptance, match count and match positions.  All inputs are seeded and synthetic."""
+import numpy as np
+import pytest
+
+import paper_1412_1741_gb300 as pm
+from oracle import oracle
+from paper_1412_1741_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+NONE = pm.PAREM_NONE
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+
+    from paper_1412_1741_gb300 import build
+
+    build.build()
+    pm.load_library()
+    assert _t.cuda.is_available()
+    return _t
+
+
+_DFA_CACHE = {}
+
+
+def load(spec):
+    key = id(spec)
+    if key not in _DFA_CACHE:
+        _DFA_CACHE[key] = (spec, pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept))
+    return _DFA_CACHE[key][1]
+
+
+def device_text(torch, text, offset=0):
+    n = int(text.size)
+    buf = torch.zeros(n + offset + 64, dtype=torch.uint8, device="cuda")
+    view = buf[offset:offset + n]
+    if n:
+        view.copy_(torch.from_numpy(np.ascontiguousarray(text)))
+    return buf, view
+
+
+def check(torch, spec, text, offset=0, opts=None, positions=True, capacity=None, start=None):
+    dfa = load(spec)
+    _, view = device_text(torch, text, offset)
+    st = spec.start if start is None else start
+    want = oracle.scan(spec.table, spec.byte_to_symbol, st, spec.accept, text, want_positions=positions)
+    cap = capacity if capacity is not None else max(want.match_count, 1)
+    pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda") if positions else None
+    if opts is None and start is None:
+        got = pm.parem_match(dfa, view, pos, length=text.size)
+    else:
+        o = opts or pm.MatchOpts()
+        if start is not None:
+            o.start_state = start
+        got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
+    assert got.final_state == want.final_state
+    assert got.accepted == want.accepted
+    assert got.match_count == want.match_count
+    if positions:
+        k = min(cap, want.match_count)
+        assert got.n_written == k
+        g = pos[:k].cpu().numpy().astype(np.uint64)
+        assert np.array_equal(g, want.positions[:k])
+        if want.match_count > cap:
+            assert got.status == -3
+    return got, want
+
+
+def random_partial(seed, n, k, p_none=0.1, b2s_frac=0.9):
+    rng = np.random.default_rng(seed)
+    t = rng.integers(0, n, size=(n, k)).astype(np.uint32)
+    t[rng.random((n, k)) < p_none] = NONE
+    acc = (rng.random(n) < 0.2).astype(np.uint8)
+    b2s = np.full(256, pm.PAREM_NONE16, np.uint16)
+    keep = rng.random(256) < b2s_frac
+    b2s[keep] = rng.integers(0, k, size=int(keep.sum()))
+    return wl.DfaSpec(t, int(rng.integers(0, n)), acc, b2s, f"partial{seed}")
+
+
+# ---------------------------------------------------------------------------------------
+GATTACA = wl.gattaca_dfa()
+PARALLEL = wl.parallel_dfa()
+AC = wl.keywords_ac_dfa()
+DENSE = wl.dense_dfa()
+PARITY = wl.DfaSpec(np.array([[1, 0], [0, 1]], np.uint32), 0, np.array([1, 0], np.uint8), None, "parity")
+MOD3 = wl.DfaSpec(np.array([[(2 * q + a) % 3 for a in range(2)] for q in range(3)], np.uint32), 0,
+                  np.array([1, 0, 0], np.uint8), None, "mod3")
+
+
+def test_paper_worked_example(torch):
+    text = np.frombuffer(bytes(wl.PARALLEL_ALPHABET.index(c) for c in b"plaraparallelapareparapl"), np.uint8)
+    got, want = check(torch, PARALLEL, text)
+    assert (got.match_count, want.positions.tolist()) == (1, [12])
+
+
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 100, 143, 144, 145, 1000, 4095, 4096, 4097, 65549, 300001])
+@pytest.mark.parametrize("offset", [0, 1, 7, 15])
+def test_lengths_and_alignments_gattaca(torch, n, offset):
+    check(torch, GATTACA, wl.uniform_text(n, 4, seed=n + offset), offset=offset)
+
+
+@pytest.mark.parametrize("seg", [128, 256, 384, 2048])
+@pytest.mark.parametrize("spec", [GATTACA, PARALLEL, AC, DENSE], ids=lambda s: s.name)
+def test_many_chunks_forced_segments(torch, spec, seg):
+    n = 200_000 + 37
+    if spec is AC:
+        text = wl.zipf_words_text(n, plant_rate=3e-4)
+    elif spec is DENSE:
+        text = wl.uniform_text(n, 256, seed=5)
+    else:
+        text = wl.uniform_text(n, spec.n_symbols, seed=seg)
+    check(torch, spec, text, offset=3, opts=pm.MatchOpts(segment_bytes=seg))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_partial_dfas_with_dead_states(torch, seed):
+    spec = random_partial(seed, n=int(np.random.default_rng(seed).integers(2, 40)), k=3, p_none=0.02 * seed)
+    rng = np.random.default_rng(100 + seed)
+    text = rng.integers(0, 256, size=150_000, dtype=np.uint8)
+    check(torch, spec, text, opts=pm.MatchOpts(segment_bytes=256))
+    check(torch, spec, text[:5000], offset=5)
+
+
+@pytest.mark.parametrize("spec", [PARITY, MOD3], ids=lambda s: s.name)
+def test_non_converging_dfas_use_slot_maps(torch, spec):
+    text = wl.uniform_text(120_000 + 5, 2, seed=1)
+    check(torch, spec, text, opts=pm.MatchOpts(segment_bytes=128))
+    check(torch, spec, text, opts=pm.MatchOpts(segment_bytes=1024), offset=9)
+
+
+def test_more_candidates_than_registers(torch):
+    # 1200 states over 4 symbols: |img(c)| ~ 760 > 256 candidates held in registers
+    t, acc = wl.random_dfa(1200, 4, 100, seed=21)
+    spec = wl.DfaSpec(t, 0, acc, None, "rand1200")
+    text = wl.uniform_text(40_000, 4, seed=2)
+    check(torch, spec, text, opts=pm.MatchOpts(segment_bytes=256))
+
+
+def test_large_table_in_global_memory(torch):
+    t, acc = wl.random_dfa(3000, 40, 300, seed=22)  # 3000 x 40 x 2 B > shared-memory budget
+    spec = wl.DfaSpec(t, 0, acc, None, "rand3000")
+    assert pm.parem_prepare_info(t, None, 0, acc).layout == 2
+    check(torch, spec, wl.uniform_text(300_000, 40, seed=3), opts=pm.MatchOpts(segment_bytes=4096))
+
+
+@pytest.mark.parametrize("spec", [GATTACA, PARALLEL], ids=lambda s: s.name)
+def test_enumeration_mode(torch, spec):
+    text = wl.uniform_text(100_000, spec.n_symbols, seed=4)
+    check(torch, spec, text, opts=pm.MatchOpts(enumerate_all=1, segment_bytes=256))
+
+
+def test_carry_in_start_state(torch):
+    text = wl.uniform_text(250_000, 4, seed=6)
+    whole = oracle.scan(GATTACA.table, None, 0, GATTACA.accept, text)
+    cut = 123_457
+    a, _ = check(torch, GATTACA, text[:cut])
+    b, _ = check(torch, GATTACA, text[cut:], start=a.final_state, opts=pm.MatchOpts(segment_bytes=512))
+    assert a.match_count + b.match_count == whole.match_count
+    assert b.final_state == whole.final_state
+
+
+def test_capacity_and_count_only(torch):
+    text = wl.uniform_text(500_000, 4, seed=7)
+    got, want = check(torch, GATTACA, text, capacity=5)
+    assert got.status == -3 and got.n_written == 5
+    got, _ = check(torch, GATTACA, text, positions=False)
+    assert got.n_written == 0
+
+
+def test_zipf_words_ac_64mb(torch):
+    text = wl.zipf_words_text(64 << 20)
+    check(torch, AC, text, offset=1)
+
+
+def test_dense_64mb(torch):
+    text = wl.uniform_text(64 << 20, 256, seed=5)
+    check(torch, DENSE, text, offset=2)
+
+
+def test_timeout_hook_reports_error_and_context_survives(torch):
+    text = wl.uniform_text(300_000, 4, seed=8)
+    dfa = load(GATTACA)
+    _, view = device_text(torch, text)
+    o = pm.MatchOpts(segment_bytes=128, debug_skip_publish_chunk=3, wait_budget_cycles=200_000_000)
+    with pytest.raises(pm.ParemError) as e:
+        pm.parem_match_ex(dfa, view, None, o, length=text.size)
+    assert e.value.status == -4
+    check(torch, GATTACA, text)  # the context is still usable
+
+
+def test_host_buffers(torch):
+    text = wl.uniform_text(1 << 20, 4, seed=0)
+    want = oracle.scan(GATTACA.table, None, 0, GATTACA.accept, text)
+    pos = np.zeros(max(1, want.match_count), np.uint64)
+    got = pm.parem_match_host(load(GATTACA), text, pos)
+    assert (got.final_state, got.match_count) == (want.final_state, want.match_count)
+    assert np.array_equal(pos[:got.n_written], want.positions)
