@@ -75,7 +75,8 @@ typedef struct {
   uint32_t has_dead;        /* 1 when a dead state was added */
   uint32_t entry_bytes;     /* 1 (<= 256 compact states) or 2 */
   uint32_t layout;          /* 0: byte-indexed table in shared memory, 1: class-indexed table
-                               in shared memory, 2: class-indexed table in global memory (L2) */
+                               in shared memory, 2: class-indexed table in global memory (L2);
+                               3 and 4: as 1 and 2 with 2-byte column offsets */
   uint32_t table_bytes;     /* bytes of the device transition table */
   uint32_t max_candidates;  /* largest candidate set |img(c) \ {dead}| over classes */
   uint32_t reserved;
@@ -101,7 +102,26 @@ typedef struct {
   int64_t debug_skip_publish_chunk; /* test hook, -1 = off: the chunk with this index never
                                        publishes its state, so its successor's bounded wait
                                        runs out and the call returns PAREM_ERR_TIMEOUT */
+  uint32_t record_kernel_times; /* 1: record CUDA events around each kernel of the call on the
+                                   call's stream; read them with parem_last_stats */
+  uint32_t reserved;
 } parem_match_opts;
+
+/* What the last scan on a (device, stream) did: its plan and, when record_kernel_times was
+ * set, the device time of each kernel. */
+typedef struct {
+  float scan_ms;            /* pass 1: speculation, main run and look-back (-1 if not timed) */
+  float emit_ms;            /* pass 2: position emission (0 if not launched, -1 if not timed) */
+  uint64_t segment_bytes;   /* S: bytes per lane segment */
+  uint64_t rows;            /* full segments */
+  uint64_t chunks;          /* 32-segment chunks (look-back units) */
+  uint32_t blocks;          /* persistent thread blocks of pass 1 */
+  uint32_t warps_per_block;
+  uint32_t candidate_regs;  /* candidate registers per lane in the speculation (1 or 8) */
+  uint32_t spec_cap_bytes;  /* longest speculative prefix per segment */
+  uint32_t kernels;         /* kernels launched by the call */
+  uint32_t reserved;
+} parem_stats;
 
 /*
  * parem_load_dfa -- prepare a DFA (Q, Sigma, delta, q0, F) (Section II-A) and upload it
@@ -168,6 +188,10 @@ int parem_match_ex(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint
  */
 int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                      uint64_t capacity, void* stream, parem_result* out);
+
+/* Plan and kernel times of the last scan issued on (current device, stream); waits for the
+ * recorded events.  Errors: INVALID_ARG (no scan yet), CUDA. */
+int parem_last_stats(void* stream, parem_stats* out);
 
 /* Release the scratch memory cached for (current device, stream).  Errors: CUDA. */
 int parem_release_scratch(void* stream);

@@ -25,7 +25,7 @@ __all__ = [
     "PAREM_NONE", "PAREM_NONE16", "ParemError", "MatchResult", "DfaInfo", "Dfa", "MatchOpts",
     "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa",
     "parem_match", "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror",
-    "parem_version", "EXPORTED_SYMBOLS",
+    "parem_version", "parem_last_stats", "Stats", "EXPORTED_SYMBOLS",
 ]
 
 PAREM_NONE = 0xFFFFFFFF
@@ -40,6 +40,7 @@ _LIB = None
 EXPORTED_SYMBOLS = [
     "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
+    "parem_last_stats",
 ]
 
 
@@ -68,12 +69,23 @@ class MatchOpts(ctypes.Structure):
     _fields_ = [("start_state", ctypes.c_uint32), ("enumerate_all", ctypes.c_uint32),
                 ("segment_bytes", ctypes.c_uint64), ("warps_per_block", ctypes.c_uint32),
                 ("spec_cap_bytes", ctypes.c_uint32), ("wait_budget_cycles", ctypes.c_uint64),
-                ("debug_skip_publish_chunk", ctypes.c_int64)]
+                ("debug_skip_publish_chunk", ctypes.c_int64), ("record_kernel_times", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
     def __init__(self, start_state=PAREM_NONE, enumerate_all=0, segment_bytes=0, warps_per_block=0,
-                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=-1):
+                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=-1, record_kernel_times=0):
         super().__init__(start_state, enumerate_all, segment_bytes, warps_per_block, spec_cap_bytes,
-                         wait_budget_cycles, debug_skip_publish_chunk)
+                         wait_budget_cycles, debug_skip_publish_chunk, record_kernel_times, 0)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("scan_ms", ctypes.c_float), ("emit_ms", ctypes.c_float), ("segment_bytes", ctypes.c_uint64),
+                ("rows", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("blocks", ctypes.c_uint32),
+                ("warps_per_block", ctypes.c_uint32), ("candidate_regs", ctypes.c_uint32),
+                ("spec_cap_bytes", ctypes.c_uint32), ("kernels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 @dataclass
@@ -126,11 +138,12 @@ def load_library(build_if_missing: bool = False):
     lib.parem_match_ex.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(MatchOpts), vp, ctypes.POINTER(_Result)]
     lib.parem_match_host.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
     lib.parem_release_scratch.argtypes = [vp]
+    lib.parem_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.parem_strerror.argtypes = [ctypes.c_int]
     lib.parem_strerror.restype = ctypes.c_char_p
     lib.parem_version.restype = ctypes.c_char_p
     for f in ("parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_match", "parem_match_ex",
-              "parem_match_host", "parem_release_scratch"):
+              "parem_match_host", "parem_release_scratch", "parem_last_stats"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -284,3 +297,12 @@ def parem_release_scratch(stream=None) -> None:
     rc = load_library().parem_release_scratch(_stream(stream))
     if rc != PAREM_OK:
         raise ParemError(rc, "parem_release_scratch")
+
+
+def parem_last_stats(stream=None) -> dict:
+    """Plan and (when record_kernel_times was set) kernel times of the last scan on a stream."""
+    st = Stats()
+    rc = load_library().parem_last_stats(_stream(stream), ctypes.byref(st))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_last_stats")
+    return st.as_dict()

@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <utility>
+#include <vector>
 
 #include "../../include/parem.h"
 #include "parem_internal.h"
@@ -49,6 +50,9 @@ struct Scratch {
   size_t text_bytes = 0;
   void* dev_pos = nullptr;
   size_t pos_bytes = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before pass 1, after pass 1, after emit
+  bool timed = false, emitted = false, have_stats = false;
+  parem_stats stats{};
 };
 
 std::mutex g_mu;
@@ -102,7 +106,7 @@ int encode_rows(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R) {
   cuuint32_t box[2] = {kBox, kLanes};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(base), dims, strides, box,
-                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? PAREM_OK : PAREM_ERR_CUDA;
 }
@@ -198,7 +202,16 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
     return o;
   };
   const size_t o_table = take(P.table.size());
-  const size_t o_colmap = take(256 * 4);
+  const bool wide = P.layout == kClassSmemW || P.layout == kClassGlobalW;
+  std::vector<uint8_t> cm(512, 0);
+  for (int b = 0; b < 256; ++b) {
+    if (wide) {
+      std::memcpy(&cm[2 * b], &P.colmap[b], 2);
+    } else {
+      cm[b] = (uint8_t)P.colmap[b];
+    }
+  }
+  const size_t o_colmap = take(512);
   const size_t o_cls = take(256 * 2);
   const size_t o_imgoff = take(P.img_off.size() * 4);
   const size_t o_img = take(P.img.size() * 2);
@@ -210,7 +223,7 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
   uint8_t* base = static_cast<uint8_t*>(d->dmem);
   cudaError_t e = cudaSuccess;
   e = e == cudaSuccess ? cudaMemcpy(base + o_table, P.table.data(), P.table.size(), cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_colmap, P.colmap.data(), 256 * 4, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_colmap, cm.data(), 512, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cudaMemcpy(base + o_cls, P.byte_class.data(), 256 * 2, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cudaMemcpy(base + o_imgoff, P.img_off.data(), P.img_off.size() * 4, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cudaMemcpy(base + o_img, P.img.data(), P.img.size() * 2, cudaMemcpyHostToDevice) : e;
@@ -222,7 +235,7 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
   }
   DeviceDfa& D = d->dev;
   D.table = base + o_table;
-  D.colmap = reinterpret_cast<const uint32_t*>(base + o_colmap);
+  D.colmap = base + o_colmap;
   D.byte_class = reinterpret_cast<const uint16_t*>(base + o_cls);
   D.img_off = reinterpret_cast<const uint32_t*>(base + o_imgoff);
   D.img = reinterpret_cast<const uint16_t*>(base + o_img);
@@ -255,6 +268,33 @@ extern "C" void parem_free_dfa(parem_dfa* dfa) {
   delete dfa;
 }
 
+extern "C" int parem_last_stats(void* stream, parem_stats* out) {
+  if (!out) return PAREM_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
+  Scratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_scratch.find({dev, stream});
+    if (it == g_scratch.end()) return PAREM_ERR_INVALID_ARG;
+    s = it->second;
+  }
+  if (!s->have_stats) return PAREM_ERR_INVALID_ARG;
+  *out = s->stats;
+  out->scan_ms = -1.f;
+  out->emit_ms = -1.f;
+  if (s->timed) {
+    PAREM_CUDA_TRY(cudaEventSynchronize(s->ev[2]));
+    PAREM_CUDA_TRY(cudaEventElapsedTime(&out->scan_ms, s->ev[0], s->ev[1]));
+    if (s->emitted) {
+      PAREM_CUDA_TRY(cudaEventElapsedTime(&out->emit_ms, s->ev[1], s->ev[2]));
+    } else {
+      out->emit_ms = 0.f;
+    }
+  }
+  return PAREM_OK;
+}
+
 extern "C" int parem_release_scratch(void* stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
@@ -271,6 +311,8 @@ extern "C" int parem_release_scratch(void* stream) {
   if (s->dev_text) cudaFree(s->dev_text);
   if (s->dev_pos) cudaFree(s->dev_pos);
   if (s->host_res) cudaFreeHost(s->host_res);
+  for (auto& ev : s->ev)
+    if (ev) cudaEventDestroy(ev);
   delete s;
   return PAREM_OK;
 }
@@ -287,34 +329,24 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   std::memset(pl, 0, sizeof(*pl));
   pl->enum_all = o && o->enumerate_all ? 1u : 0u;
   const uint32_t m_need = pl->enum_all ? (P.n - P.has_dead) : P.max_cand;
-  pl->P = m_need <= 32 ? 1 : 8;
+  pl->P = m_need <= 32 ? 1 : m_need <= 64 ? 2 : m_need <= 128 ? 4 : 8;
   pl->cand_stride = std::max<uint32_t>(1, std::max(P.max_cand, pl->enum_all ? P.n : 0u));
-  // shared memory carve-up of pass 1
-  const uint32_t per_warp_stage = kStages * kStageBytes;
-  const uint32_t per_warp_hash = pl->P > 1 ? kHashSize * 4 : 0;
-  const uint32_t table_smem = P.layout == kClassGlobal ? 0 : P.table_bytes;
-  const uint32_t fixed = 1024 /*align slack*/ + 1024 /*colmap*/ + table_smem + 256;
-  const uint32_t per_warp = per_warp_stage + kStages * 8 + per_warp_hash;
+  // lanes per row in the grouped speculation (P == 1): the smallest power of two that holds
+  // the largest candidate set
+  pl->group = 1;
+  while (pl->group < m_need && pl->group < 32) pl->group *= 2;
+  // shared memory of pass 1: [colmap | table at kTableOff][slack to 1024][per-warp region]
+  const uint32_t table_smem = (P.layout == kClassGlobal || P.layout == kClassGlobalW) ? 0 : P.table_bytes;
+  pl->table_smem = table_smem;
+  const uint32_t fixed = kTableOff + table_smem + 1024;
+  const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + kSpecBytes;
   int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
   warps = std::min(warps, 32);
   if (o && o->warps_per_block) warps = std::min<int>(warps, (int)o->warps_per_block);
   if (warps < 1) return PAREM_ERR_UNSUPPORTED;
   pl->warps = warps;
   pl->grid = props.sms;
-  uint32_t off = 0;
-  pl->stage_off = off;
-  off += warps * per_warp_stage;
-  pl->bar_off = off;
-  off += warps * kStages * 8;
-  off = (uint32_t)round_up(off, 16);
-  pl->hash_off = off;
-  off += warps * per_warp_hash;
-  off = (uint32_t)round_up(off, 16);
-  pl->colmap_off = off;
-  off += 1024;
-  pl->table_off = off;
-  off += table_smem;
-  pl->smem = off + 1024;
+  pl->smem = fixed + (size_t)warps * per_warp;
   // rows
   const uint64_t addr = reinterpret_cast<uint64_t>(text);
   pl->h = std::min<uint64_t>(len, (16 - (addr & 15)) & 15);
@@ -390,6 +422,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.tail = pl.tail;
   p.n_chunks = pl.n_chunks;
   p.init_state = init;
+  p.group = pl.group;
+  p.smem_table_bytes = pl.table_smem;
   p.enum_all = pl.enum_all;
   p.spec_cap = pl.spec_cap;
   p.cand_stride = pl.cand_stride;
@@ -405,31 +439,42 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.positions = emit ? positions : nullptr;
   p.capacity = emit ? capacity : 0;
 
-  const size_t small_smem = 1024 + (P.layout == kClassGlobal ? 0 : P.table_bytes);
+  const bool global_table = P.layout == kClassGlobal || P.layout == kClassGlobalW;
+  const size_t small_smem = kTableOff + (global_table ? 0 : P.table_bytes);
+  const bool timed = o && o->record_kernel_times;
+  if (timed && !sc->ev[0]) {
+    for (auto& ev : sc->ev) PAREM_CUDA_TRY(cudaEventCreate(&ev));
+  }
+  sc->timed = timed;
+  sc->emitted = false;
+  sc->have_stats = true;
+  sc->stats = parem_stats{};
+  sc->stats.segment_bytes = pl.S;
+  sc->stats.rows = pl.R;
+  sc->stats.chunks = pl.n_chunks;
+  sc->stats.blocks = pl.R ? (uint32_t)pl.grid : 1;
+  sc->stats.warps_per_block = pl.R ? (uint32_t)pl.warps : 1;
+  sc->stats.candidate_regs = pl.P;
+  sc->stats.spec_cap_bytes = pl.spec_cap;
+  sc->stats.kernels = 1 + ((pl.R && emit) ? 1 : 0);
+  if (timed) PAREM_CUDA_TRY(cudaEventRecord(sc->ev[0], stream));
   cudaError_t e;
   if (pl.R == 0) {
-    ScanParams q = p;
-    q.smem_colmap_off = 0;
-    q.smem_table_off = 1024;
-    e = launch_tiny_dispatch(P.layout, P.esize, q, small_smem, stream);
+    e = launch_tiny_dispatch(P.layout, P.esize, p, small_smem, stream);
   } else {
     CUtensorMap tm;
     rc = encode_rows(&tm, text + pl.h, pl.S, pl.R);
     if (rc != PAREM_OK) return rc;
-    p.smem_stage_off = pl.stage_off;
-    p.smem_bar_off = pl.bar_off;
-    p.smem_hash_off = pl.hash_off;
-    p.smem_colmap_off = pl.colmap_off;
-    p.smem_table_off = pl.table_off;
     e = launch_scan_dispatch(P.layout, P.esize, pl.P, tm, p, pl.grid, pl.warps * 32, pl.smem, stream);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(sc->ev[1], stream);
     if (e == cudaSuccess && emit) {
-      ScanParams q = p;
-      q.smem_colmap_off = 0;
-      q.smem_table_off = 1024;
+      sc->emitted = true;
       const DevProps props = dev_props(dfa->device);
-      e = launch_emit_dispatch(P.layout, P.esize, q, props.sms * 4, 256, small_smem, stream);
+      e = launch_emit_dispatch(P.layout, P.esize, p, props.sms * 4, 256, small_smem, stream);
     }
   }
+  if (e == cudaSuccess && timed && pl.R == 0) e = cudaEventRecord(sc->ev[1], stream);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(sc->ev[2], stream);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
   PAREM_CUDA_TRY(cudaMemcpyAsync(sc->host_res, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, stream));
   PAREM_CUDA_TRY(cudaStreamSynchronize(stream));

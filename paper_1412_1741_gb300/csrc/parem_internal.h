@@ -10,16 +10,24 @@
 namespace parem {
 
 constexpr uint32_t kLanes = 32;          // segments per chunk: one per lane of the owning warp
-constexpr uint32_t kBox = 128;           // bytes of one TMA column block per row (128B swizzle)
+constexpr uint32_t kBox = 64;            // bytes of one TMA column block per row (64B swizzle)
 constexpr uint32_t kStages = 2;          // TMA stages per warp
-constexpr uint32_t kStageBytes = kLanes * kBox;  // 4 KiB: 32 rows x 128 B
+constexpr uint32_t kStageBytes = kLanes * kBox;  // 2 KiB: 32 rows x 64 B
 constexpr uint32_t kEmpty = 0xFFFFFFFFu; // an empty candidate register / "no state"
 constexpr uint32_t kNoSlot = 0xFFFFu;    // rank(c, q) when q is not a candidate of class c
-constexpr uint32_t kHashSize = 512;      // per-warp owner table used to merge candidates (P > 1)
+constexpr uint32_t kLaneCand = 8;        // survivors a lane takes over from the warp-wide phase
+// per-warp speculation scratch in shared memory: hand-over lists (32 rows x 8 states, u16)
+// followed by a 32-word compaction buffer
+constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4;
+constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
 constexpr uint64_t kMaxText = 1ull << 45;
 
-// Table layouts (parem_dfa_info.layout).
-enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2 };
+// Table layouts (parem_dfa_info.layout).  The class layouts read a 256-entry byte -> column
+// map; its entries are u8 when every column offset fits a byte, else u16 (the *W layouts).
+enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClassSmemW = 3, kClassGlobalW = 4 };
+// Shared memory of every kernel starts with the column map (512 B reserved) followed by the
+// table at this fixed offset, so table reads use an immediate offset.
+constexpr uint32_t kTableOff = 512;
 
 // Chunk status word (64 bit), published with release semantics:
 //   [63:62] flag  0 none, 1 MAPPED (end state E known), 2 AGGREGATE (E, dead, count),
@@ -48,7 +56,7 @@ struct Prepared {
   std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
   std::vector<uint32_t> compact_of; // original -> compact
   std::vector<uint16_t> byte_class; // 256
-  std::vector<uint32_t> colmap;     // 256: column byte offset of each byte in a table row
+  std::vector<uint16_t> colmap;     // 256: column byte offset of each byte in a table row
   std::vector<uint8_t> table;       // n * rowbytes (padded to 16)
   std::vector<uint32_t> img_off;    // n_classes + 2 offsets; list n_classes = all live states
   std::vector<uint16_t> img;        // candidate lists, sorted, dead excluded
@@ -63,7 +71,7 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
 // Device-resident DFA, passed by value to kernels.
 struct DeviceDfa {
   const uint8_t* table;
-  const uint32_t* colmap;
+  const uint8_t* colmap;          // 256 entries of 1 or 2 bytes (layout)
   const uint16_t* byte_class;
   const uint32_t* img_off;
   const uint16_t* img;
@@ -72,11 +80,17 @@ struct DeviceDfa {
   uint32_t layout, esize, rowbytes, table_bytes, max_cand;
 };
 
-// Per-segment record for the emit pass.
+// Per-segment record for the emit pass: the matches of the row lie in the row-relative
+// window [fv, lv), which the emit pass re-runs from state fs.
 struct SegRec {
-  uint32_t x;       // true compact start state of the segment (dead -> DeviceDfa::dead / kEmpty)
+  uint32_t fs;      // state at row offset fv (or, with kHeadFlag, the start before the head)
   uint32_t count;   // matches inside the segment
   uint64_t offset;  // index of the segment's first match in the global position order
+  uint32_t fv, lv;  // window (row-relative bytes; the last row extends into the tail)
+  uint32_t lvv, ls; // last matching vector [lvv, lv) and the state at lvv (fast replay)
+  uint32_t x;       // true start state of the row
+  uint32_t flags;
+  uint32_t pad[2];
 };
 
 // Result word filled on the device.
@@ -97,6 +111,7 @@ struct ScanParams {
   uint64_t tail;           // bytes after the last full row, appended to row R-1
   uint64_t n_chunks;       // ceil(R / 32)
   uint32_t init_state;     // compact start state (q0 or carried in)
+  uint32_t group;          // lanes per row in the speculation when P == 1 (power of two <= 32)
   uint32_t enum_all;       // candidates = all live states
   uint32_t spec_cap;       // bytes of speculation before a segment counts as non-converged
   uint32_t cand_stride;    // slots per segment in the slot map
@@ -112,8 +127,9 @@ struct ScanParams {
   // outputs
   uint64_t* positions;
   uint64_t capacity;
-  // shared memory carve-up (bytes from the dynamic smem base)
-  uint32_t smem_stage_off, smem_bar_off, smem_hash_off, smem_colmap_off, smem_table_off;
+  // shared memory: [colmap | table at kTableOff] then, from the first 1024-aligned address
+  // at or after kTableOff + smem_table_bytes: per-warp stages, barriers and speculation scratch
+  uint32_t smem_table_bytes;
 };
 
 }  // namespace parem

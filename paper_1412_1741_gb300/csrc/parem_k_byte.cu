@@ -6,11 +6,16 @@ namespace parem {
 
 cudaError_t scan_byte(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
                       int block, size_t smem, cudaStream_t s) {
-  if (esize == 1)
-    return P == 1 ? launch_spec_scan<kByteSmem, 1, 1>(tm, p, grid, block, smem, s)
-                  : launch_spec_scan<kByteSmem, 1, 8>(tm, p, grid, block, smem, s);
-  return P == 1 ? launch_spec_scan<kByteSmem, 2, 1>(tm, p, grid, block, smem, s)
-                : launch_spec_scan<kByteSmem, 2, 8>(tm, p, grid, block, smem, s);
+  switch (esize * 16 + P) {
+    case 16 + 1: return launch_spec_scan<kByteSmem, 1, 1>(tm, p, grid, block, smem, s);
+    case 16 + 2: return launch_spec_scan<kByteSmem, 1, 2>(tm, p, grid, block, smem, s);
+    case 16 + 4: return launch_spec_scan<kByteSmem, 1, 4>(tm, p, grid, block, smem, s);
+    case 16 + 8: return launch_spec_scan<kByteSmem, 1, 8>(tm, p, grid, block, smem, s);
+    case 32 + 1: return launch_spec_scan<kByteSmem, 2, 1>(tm, p, grid, block, smem, s);
+    case 32 + 2: return launch_spec_scan<kByteSmem, 2, 2>(tm, p, grid, block, smem, s);
+    case 32 + 4: return launch_spec_scan<kByteSmem, 2, 4>(tm, p, grid, block, smem, s);
+    default: return launch_spec_scan<kByteSmem, 2, 8>(tm, p, grid, block, smem, s);
+  }
 }
 
 cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {

@@ -5,21 +5,31 @@
 
 namespace parem {
 
-cudaError_t scan_global(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+cudaError_t scan_global(uint32_t wide, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
                         int block, size_t smem, cudaStream_t s) {
-  (void)esize;
-  return P == 1 ? launch_spec_scan<kClassGlobal, 2, 1>(tm, p, grid, block, smem, s)
-                : launch_spec_scan<kClassGlobal, 2, 8>(tm, p, grid, block, smem, s);
+  if (wide) {
+    switch (P) {
+      case 1: return launch_spec_scan<kClassGlobalW, 2, 1>(tm, p, grid, block, smem, s);
+      case 2: return launch_spec_scan<kClassGlobalW, 2, 2>(tm, p, grid, block, smem, s);
+      case 4: return launch_spec_scan<kClassGlobalW, 2, 4>(tm, p, grid, block, smem, s);
+      default: return launch_spec_scan<kClassGlobalW, 2, 8>(tm, p, grid, block, smem, s);
+    }
+  }
+  switch (P) {
+    case 1: return launch_spec_scan<kClassGlobal, 2, 1>(tm, p, grid, block, smem, s);
+    case 2: return launch_spec_scan<kClassGlobal, 2, 2>(tm, p, grid, block, smem, s);
+    case 4: return launch_spec_scan<kClassGlobal, 2, 4>(tm, p, grid, block, smem, s);
+    default: return launch_spec_scan<kClassGlobal, 2, 8>(tm, p, grid, block, smem, s);
+  }
 }
 
-cudaError_t emit_global(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  (void)esize;
-  return launch_emit<kClassGlobal, 2>(p, grid, block, smem, s);
+cudaError_t emit_global(uint32_t wide, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
+  return wide ? launch_emit<kClassGlobalW, 2>(p, grid, block, smem, s)
+              : launch_emit<kClassGlobal, 2>(p, grid, block, smem, s);
 }
 
-cudaError_t tiny_global(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s) {
-  (void)esize;
-  return launch_tiny<kClassGlobal, 2>(p, smem, s);
+cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s) {
+  return wide ? launch_tiny<kClassGlobalW, 2>(p, smem, s) : launch_tiny<kClassGlobal, 2>(p, smem, s);
 }
 
 cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, const CUtensorMap& tm,
@@ -27,7 +37,9 @@ cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, co
   switch (layout) {
     case kByteSmem: return scan_byte(esize, P, tm, p, grid, block, smem, s);
     case kClassSmem: return scan_class(esize, P, tm, p, grid, block, smem, s);
-    default: return scan_global(esize, P, tm, p, grid, block, smem, s);
+    case kClassSmemW: return scan_class_wide(P, tm, p, grid, block, smem, s);
+    case kClassGlobal: return scan_global(0, P, tm, p, grid, block, smem, s);
+    default: return scan_global(1, P, tm, p, grid, block, smem, s);
   }
 }
 
@@ -36,7 +48,9 @@ cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return emit_byte(esize, p, grid, block, smem, s);
     case kClassSmem: return emit_class(esize, p, grid, block, smem, s);
-    default: return emit_global(esize, p, grid, block, smem, s);
+    case kClassSmemW: return emit_class_wide(p, grid, block, smem, s);
+    case kClassGlobal: return emit_global(0, p, grid, block, smem, s);
+    default: return emit_global(1, p, grid, block, smem, s);
   }
 }
 
@@ -45,7 +59,9 @@ cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return tiny_byte(esize, p, smem, s);
     case kClassSmem: return tiny_class(esize, p, smem, s);
-    default: return tiny_global(esize, p, smem, s);
+    case kClassSmemW: return tiny_class_wide(p, smem, s);
+    case kClassGlobal: return tiny_global(0, p, smem, s);
+    default: return tiny_global(1, p, smem, s);
   }
 }
 

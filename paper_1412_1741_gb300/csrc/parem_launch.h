@@ -11,11 +11,12 @@ struct parem_dfa;
 namespace parem {
 
 struct Plan {
-  uint32_t P;            // candidate registers per lane (1 or 8)
+  uint32_t P;            // candidate registers per lane in the warp-wide phase (1, 2, 4, 8)
   uint32_t enum_all;
   uint32_t cand_stride;
+  uint32_t group;        // lanes per row in the grouped speculation (P == 1)
   int warps, grid;
-  uint32_t stage_off, bar_off, hash_off, colmap_off, table_off;
+  uint32_t table_smem;   // table bytes staged in shared memory (0 for the global layouts)
   size_t smem;
   uint64_t h, S, R, tail, n_chunks;
   uint32_t spec_cap;
@@ -33,13 +34,17 @@ cudaError_t scan_byte(uint32_t esize, uint32_t P, const CUtensorMap& tm, const S
                       int block, size_t smem, cudaStream_t s);
 cudaError_t scan_class(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
                        int block, size_t smem, cudaStream_t s);
-cudaError_t scan_global(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
+cudaError_t scan_class_wide(uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid, int block,
+                            size_t smem, cudaStream_t s);
+cudaError_t scan_global(uint32_t wide, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
                         int block, size_t smem, cudaStream_t s);
 cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t emit_class(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t emit_global(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_class_wide(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_global(uint32_t wide, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
-cudaError_t tiny_global(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t tiny_class_wide(const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s);
 
 }  // namespace parem

@@ -174,6 +174,9 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
     P.layout = kClassGlobal;
     P.rowbytes = rb_cls;
   }
+  // column offsets that do not fit a byte need the wide column map
+  if (P.layout != kByteSmem && (P.n_classes - 1) * P.esize > 255)
+    P.layout = P.layout == kClassSmem ? kClassSmemW : kClassGlobalW;
   uint64_t tbytes = (uint64_t)n * P.rowbytes;
   tbytes = (tbytes + 15) & ~15ull;
   if (tbytes > 0xFFFFFFFFull) return PAREM_ERR_UNSUPPORTED;
@@ -193,12 +196,12 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
     for (int b = 0; b < 256; ++b) {
       const auto& col = cols[P.byte_class[b]];
       for (uint32_t s = 0; s < n; ++s) put(s, (uint32_t)b * P.esize, col[s]);
-      P.colmap[b] = (uint32_t)b * P.esize;
+      P.colmap[b] = (uint16_t)(b * P.esize);
     }
   } else {
     for (uint32_t c = 0; c < P.n_classes; ++c)
       for (uint32_t s = 0; s < n; ++s) put(s, c * P.esize, cols[c][s]);
-    for (int b = 0; b < 256; ++b) P.colmap[b] = (uint32_t)P.byte_class[b] * P.esize;
+    for (int b = 0; b < 256; ++b) P.colmap[b] = (uint16_t)(P.byte_class[b] * P.esize);
   }
 
   // candidate lists and ranks; list n_classes holds every live state (enumeration mode)

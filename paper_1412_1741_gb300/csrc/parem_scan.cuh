@@ -7,20 +7,25 @@
 //   * Candidate speculation (R = S n L): for row r > 0 the candidates are img(c), the
 //     distinct states reachable on the class c of the byte that ends row r-1, minus the
 //     dead state (a dead run needs no simulation).  Row 0 starts from q0 exactly.
-//   * Candidate runs: the warp runs the candidates of one row in lockstep, one candidate per
-//     lane register, and merges lanes whose states meet (__match_any_sync, or a per-warp
-//     owner table when there are more than 32 candidates).  Once one live state is left
-//     the row's map is constant from that offset t on; the lane that owns the row then runs
-//     that single state over the rest of its row out of shared memory, where a TMA pipeline
-//     stages 32 rows x 128 bytes per step (128-byte swizzle, conflict-free reads).
+//   * Candidate runs: lanes hold candidates and advance in lockstep over the row's bytes;
+//     lanes whose states meet are merged with __match_any_sync.  Small candidate sets use
+//     G lanes per row, so 32/G rows are speculated per pass; large ones use all 32 lanes
+//     and P registers per lane for one row, compact the survivors into one register once
+//     they fit, and hand the last few (<= 8) to the lane that owns the row, all lanes then
+//     finishing their own rows in parallel.  Once one live state is left the row's map is
+//     constant from that offset t on; the lane runs that single state over the rest of its
+//     row out of shared memory, where a TMA pipeline stages 32 rows x 64 bytes per step
+//     (64-byte swizzle, conflict-free 16-byte reads).
 //   * Reduction / join: each chunk publishes its end state (MAPPED), then its match count
 //     and dead flag given the end state of the previous chunk (AGGREGATE), then the prefix
 //     (INCLUSIVE), found by a decoupled look-back over 32 predecessors at a time.  A row
 //     whose candidates never merge keeps a full slot map (end, count per candidate).
 //   * The matches inside [0, t) of each row are counted by re-running that prefix from the
 //     resolved start; the same re-run checks that the start reaches the merged state.
-//   * Emit pass: rows with matches are re-run from their resolved start and their positions
-//     are written at the row's offset in the global order.
+//   * Emit pass: pass 1 records, per row, the first and last 16-byte vectors that hold
+//     matches and the states at their starts; rows with matches replay those vectors (the
+//     whole window only when matches lie between them) and write the positions at the
+//     row's offset in the global order.
 #pragma once
 
 #include <cstdint>
@@ -92,9 +97,10 @@ __device__ __forceinline__ uint32_t ldg8(const uint8_t* p) {
   return v;
 }
 
+// byte i (0..15) of a 16-byte vector, zero-extended (one PRMT)
 __device__ __forceinline__ uint32_t byte_of(const uint4& v, int i) {
   const uint32_t w = (i < 4) ? v.x : (i < 8) ? v.y : (i < 12) ? v.z : v.w;
-  return (w >> (8 * (i & 3))) & 0xFFu;
+  return __byte_perm(w, 0u, 0x4440u + (uint32_t)(i & 3));
 }
 
 __device__ __forceinline__ void set_error(DevResult* r, uint32_t code) {
@@ -106,32 +112,48 @@ __device__ __forceinline__ uint32_t read_error(const DevResult* r) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Transition table access.  LAYOUT kByteSmem: row = 256 byte columns; kClassSmem: row =
-// class columns (byte -> column offset from colmap in smem); kClassGlobal: same in global
-// memory (read through the read-only path, L2 resident).
+// Transition table access.  The column map sits at shared offset 0 and the table (shared
+// layouts) at kTableOff, both addressed from the dynamic shared base, so a lookup is one
+// IMAD and one LDS with an immediate offset.
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE>
 struct Tab {
-  const uint8_t* sm;       // dynamic smem base (aligned)
-  uint32_t table_off;      // smem offset of the table
-  uint32_t colmap_off;     // smem offset of the 256-entry column map
-  const uint8_t* gtable;   // global table (kClassGlobal)
+  static constexpr bool kByte = LAYOUT == kByteSmem;
+  static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW;
+  static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW;
+  const uint8_t* sm;       // dynamic shared memory base
+  const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
 
   __device__ __forceinline__ uint32_t col(uint32_t b) const {
-    if (LAYOUT == kByteSmem) return b * ESIZE;
-    return reinterpret_cast<const uint32_t*>(sm + colmap_off)[b];
+    if (kByte) return b * ESIZE;
+    if (kWide) return *reinterpret_cast<const uint16_t*>(sm + 2 * b);
+    return sm[b];
   }
   __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
     const uint32_t o = s * rowbytes + c;
-    if (LAYOUT == kClassGlobal) {
+    if (kGlobal) {
       return ESIZE == 1 ? (uint32_t)__ldg(gtable + o)
                         : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(gtable + o));
     }
-    return ESIZE == 1 ? (uint32_t)sm[table_off + o]
-                      : (uint32_t)*reinterpret_cast<const uint16_t*>(sm + table_off + o);
+    return ESIZE == 1 ? (uint32_t)sm[kTableOff + o]
+                      : (uint32_t)*reinterpret_cast<const uint16_t*>(sm + kTableOff + o);
   }
 };
+
+// Stage the column map and (shared layouts) the table into shared memory.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void load_tables(uint8_t* sm, const DeviceDfa& D) {
+  const uint32_t cm_bytes = Tab<LAYOUT, ESIZE>::kWide ? 512u : 256u;
+  const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
+  uint4* dst = reinterpret_cast<uint4*>(sm);
+  for (uint32_t i = threadIdx.x; i < cm_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  if (!Tab<LAYOUT, ESIZE>::kGlobal) {
+    const uint4* ts = reinterpret_cast<const uint4*>(D.table);
+    uint4* td = reinterpret_cast<uint4*>(sm + kTableOff);
+    for (uint32_t i = threadIdx.x; i < D.table_bytes / 16; i += blockDim.x) td[i] = ts[i];
+  }
+}
 
 // Run [0, len) of a 16-byte aligned global range from state x.  Adds the matches to *cnt
 // and returns the end state; stops early (returning dead) once the run is dead.
@@ -196,32 +218,32 @@ __device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity, uint64
   return true;
 }
 
+// Offset of pass 1's per-warp region: the first 1024-aligned shared address after the
+// tables (the host reserves 1024 bytes of slack for this alignment).
+__device__ __forceinline__ uint32_t stage_region_off(const uint8_t* smem_raw, uint32_t table_bytes) {
+  const uint32_t base = smem_u32(smem_raw);
+  const uint32_t a = base + kTableOff + table_bytes;
+  return ((a + 1023u) & ~1023u) - base;
+}
+
 // ---------------------------------------------------------------------------------------
-// Pass 1: speculation, main run, look-back.  P = candidate registers per lane.
+// Pass 1: speculation, main run, look-back.  P = candidate registers per lane when one row
+// is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE, int P>
 __global__ void __launch_bounds__(1024, 1)
     k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw = smem_u32(smem_raw);
-  uint8_t* sm = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const DeviceDfa& D = p.dfa;
-
-  // stage the column map and (smem layouts) the table
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
-    uint4* dst = reinterpret_cast<uint4*>(sm + p.smem_colmap_off);
-    for (uint32_t i = threadIdx.x; i < 1024 / 16; i += blockDim.x) dst[i] = src[i];
-    if (LAYOUT != kClassGlobal) {
-      const uint4* ts = reinterpret_cast<const uint4*>(D.table);
-      uint4* td = reinterpret_cast<uint4*>(sm + p.smem_table_off);
-      for (uint32_t i = threadIdx.x; i < D.table_bytes / 16; i += blockDim.x) td[i] = ts[i];
-    }
-  }
-  const uint32_t stage0 = p.smem_stage_off + warp * (kStages * kStageBytes);
-  const uint32_t bar0 = p.smem_bar_off + warp * (kStages * 8);
-  uint32_t* hash = reinterpret_cast<uint32_t*>(sm + p.smem_hash_off) + warp * kHashSize;
+  load_tables<LAYOUT, ESIZE>(sm, D);
+  const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
+  const uint32_t stage0 = region + warp * (kStages * kStageBytes);
+  const uint32_t bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
+  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * kSpecBytes;
+  uint16_t* hand = reinterpret_cast<uint16_t*>(sm + spec0);
+  uint32_t* cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
   if (lane == 0) {
     for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + bar0 + 8 * s), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -231,14 +253,14 @@ __global__ void __launch_bounds__(1024, 1)
 
   Tab<LAYOUT, ESIZE> tab;
   tab.sm = sm;
-  tab.table_off = p.smem_table_off;
-  tab.colmap_off = p.smem_colmap_off;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
   const uint32_t dead = D.dead;  // kEmpty when the DFA has no dead state
   const uint32_t A = D.first_accept;
   const uint32_t nblk = (uint32_t)(p.S / kBox);
   const uint32_t issue_first = nblk < kStages ? nblk : kStages;
+  const uint32_t cap = p.spec_cap;
+  const unsigned lt_mask = (1u << lane) - 1u;
   uint32_t phase_bits = 0;  // expected parity of each stage barrier
   uint32_t pending = 0;     // stages issued and not yet waited
 
@@ -253,6 +275,8 @@ __global__ void __launch_bounds__(1024, 1)
     const bool active = myrow < p.R;
     const uint32_t nrows = (uint32_t)((p.R - row0) < kLanes ? (p.R - row0) : kLanes);
     const uint8_t* body = p.text + p.h;  // 16-byte aligned
+    const bool last_row = active && myrow == p.R - 1;
+    const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
 
     // 1. start the TMA pipeline for this chunk
     if (lane == 0) {
@@ -265,121 +289,289 @@ __global__ void __launch_bounds__(1024, 1)
     }
     pending |= (1u << issue_first) - 1u;
     bool failed = false;
+    for (uint32_t b = 0; b < issue_first && !failed; ++b) {
+      if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
+        set_error(p.result, kErrTimeout);
+        failed = true;
+      }
+    }
+    // 16 bytes of row k of this chunk at row offset pos (staged bytes from shared memory)
+    auto read16 = [&](uint32_t k, uint32_t pos) -> uint4 {
+      if (pos < issue_first * kBox) {
+        const uint32_t b = pos / kBox;
+        const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
+        return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
+      }
+      return ldg16(body + (row0 + k) * p.S + pos);
+    };
+    auto cand_class = [&](uint64_t r) -> uint32_t {
+      return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
+    };
 
-    // 2. speculation, one row at a time, candidates across the lanes
-    uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0;
-    const uint32_t cap = p.spec_cap;
-    for (uint32_t k = 0; k < nrows && !failed; ++k) {
-      const uint64_t r = row0 + k;
-      if (r == 0) {
-        // row 0 starts from the exact state: the initial state run over the head bytes
-        uint32_t c0 = 0;
-        const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
-        if (lane == 0) {
-          my_t = 0;
-          my_sigma = sh;
-          my_conv = 1;
-          head_cnt = c0;
-        }
-        continue;
-      }
-      const uint32_t cls = p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
-      const uint32_t off = D.img_off[cls];
-      const uint32_t m = D.img_off[cls + 1] - off;
-      if (m <= 1 || m > 32u * P) {
-        if (lane == k) {
-          my_t = 0;
-          my_conv = m <= 1;
-          my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
-          if (m > 32u * P) my_t = (uint32_t)p.S;
-        }
-        continue;
-      }
-      uint32_t st[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        const uint32_t slot = (uint32_t)i * 32u + lane;
-        st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
-      }
-      const uint8_t* rowp = body + r * p.S;
-      uint32_t pos = 0, sigma = kEmpty;
-      bool conv = false;
-      while (pos < cap) {
-        uint4 v;
-        if (pos < kStages * kBox) {
-          const uint32_t b = pos / kBox;
-          if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget,
-                          p.result)) {
-            set_error(p.result, kErrTimeout);
-            failed = true;
-            break;
-          }
-          const uint32_t ch = ((pos % kBox) / 16u) ^ (k & 7u);
-          v = *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
-        } else {
-          v = ldg16(rowp + pos);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-          for (int i2 = 0; i2 < 4; ++i2) {
-            const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              if (st[i] != kEmpty) {
-                const uint32_t s2 = tab.next(st[i], c);
-                st[i] = (s2 == dead) ? kEmpty : s2;
-              }
+    uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
+    if constexpr (P == 1) {
+      // 2. grouped speculation: G lanes per row, 32/G rows per pass
+      const uint32_t G = p.group;
+      const uint32_t rpp = kLanes / G;
+      const uint32_t gi = lane / G, gl = lane % G;
+      const unsigned gmask = (G == 32u) ? kFull : (((1u << G) - 1u) << (gi * G));
+      for (uint32_t k0 = 0; k0 < nrows && !failed; k0 += rpp) {
+        const uint32_t k = k0 + gi;
+        const bool valid = k < nrows;
+        const uint64_t r = row0 + k;
+        uint32_t st = kEmpty, hc = 0;
+        bool exact = false;
+        if (valid) {
+          if (r == 0) {
+            // row 0 starts from the exact state: the initial state run over the head bytes
+            if (gl == 0) {
+              st = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &hc);
+              if (st == dead) st = kEmpty;
             }
-          }
-          // merge lanes whose candidates met
-          if (P == 1) {
-            const unsigned grp = __match_any_sync(kFull, st[0]);
-            if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
+            exact = true;
           } else {
-#pragma unroll
-            for (int i = 0; i < P; ++i)
-              if (st[i] != kEmpty) hash[st[i] & (kHashSize - 1)] = (st[i] << 8) | ((uint32_t)i * 32u + lane);
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              if (st[i] != kEmpty) {
-                const uint32_t e = hash[st[i] & (kHashSize - 1)];
-                if ((e >> 8) == st[i] && (e & 0xFFu) != (uint32_t)i * 32u + lane) st[i] = kEmpty;
-              }
-            }
-            __syncwarp();
+            const uint32_t cls = cand_class(r);
+            const uint32_t off = D.img_off[cls];
+            const uint32_t m = D.img_off[cls + 1] - off;
+            if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
           }
         }
-        pos += 16;
-        uint32_t live = 0, holder_reg = 0, holder_mask = 0;
+        // a row whose group has at most one live lane is already merged at t = 0
+        unsigned live = __ballot_sync(kFull, st != kEmpty);
+        bool done = exact || !valid || __popc(live & gmask) <= 1;
+        uint32_t pos = 0, outcome = 1;
+        while (!__all_sync(kFull, done)) {
+          if (!done && pos >= cap) {
+            done = true;
+            outcome = 3;
+          }
+          const uint4 v = read16(valid ? k : 0u, pos);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int i2 = 0; i2 < 4; ++i2) {
+              if (!done && st != kEmpty) {
+                const uint32_t s2 = tab.next(st, tab.col(byte_of(v, q * 4 + i2)));
+                st = (s2 == dead) ? kEmpty : s2;
+              }
+            }
+            const uint32_t key = st == kEmpty ? kEmpty : ((gi << 16) | st);
+            const unsigned grp = __match_any_sync(kFull, key);
+            if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
+          }
+          if (!done) pos += 16;
+          live = __ballot_sync(kFull, st != kEmpty);
+          if (!done && __popc(live & gmask) <= 1) done = true;
+        }
+        // the surviving state of each row (or dead) and the outcome go to the row's lane
+        live = __ballot_sync(kFull, st != kEmpty);
+        const unsigned mine = live & gmask;
+        const uint32_t sig = __shfl_sync(kFull, st, mine ? (uint32_t)(__ffs(mine) - 1) : gi * G);
+        const uint32_t sigma_row = mine ? sig : dead;
+        const uint32_t hcg = __shfl_sync(kFull, hc, gi * G);
+        // lane k (k in [k0, k0 + rpp)) collects from group k - k0
+        const uint32_t from = ((lane - k0) % rpp) * G;
+        const uint32_t o_sig = __shfl_sync(kFull, sigma_row, from);
+        const uint32_t o_out = __shfl_sync(kFull, outcome, from);
+        const uint32_t o_pos = __shfl_sync(kFull, pos, from);
+        const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
+        if (lane >= k0 && lane < k0 + rpp && lane < nrows) {
+          my_conv = o_out == 1;
+          my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
+          my_sigma = o_out == 1 ? o_sig : kEmpty;
+          head_cnt = o_hc;
+        }
+      }
+      if (row0 != 0 || lane != 0) head_cnt = 0;
+    } else {
+      // 2a. warp-wide speculation, one row at a time, candidates across lanes and registers
+      for (uint32_t k = 0; k < nrows && !failed; ++k) {
+        const uint64_t r = row0 + k;
+        if (r == 0) {
+          uint32_t c0 = 0;
+          const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
+          if (lane == 0) {
+            my_t = 0;
+            my_sigma = sh;
+            head_cnt = c0;
+          }
+          continue;
+        }
+        const uint32_t cls = cand_class(r);
+        const uint32_t off = D.img_off[cls];
+        const uint32_t m = D.img_off[cls + 1] - off;
+        if (m <= 1 || m > 32u * P) {
+          if (lane == k) {
+            my_t = m > 32u * P ? (uint32_t)p.S : 0u;
+            my_conv = m <= 1;
+            my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
+          }
+          continue;
+        }
+        uint32_t st[P];
+        uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-          const unsigned b = __ballot_sync(kFull, st[i] != kEmpty);
-          if (b && !holder_mask) {
-            holder_mask = b;
-            holder_reg = (uint32_t)i;
-          }
-          live += __popc(b);
+          const uint32_t slot = (uint32_t)i * 32u + lane;
+          st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
+          if ((uint32_t)i * 32u < m) lr |= 1u << i;
         }
-        if (live <= 1) {
-          conv = true;
-          if (live == 0) {
-            sigma = dead;
-          } else {
-            uint32_t val = kEmpty;
-#pragma unroll
-            for (int i = 0; i < P; ++i)
-              if ((uint32_t)i == holder_reg) val = st[i];
-            sigma = __shfl_sync(kFull, val, __ffs(holder_mask) - 1);
+        uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
+        for (;;) {
+          if (pos >= cap) {
+            outcome = 3;
+            break;
           }
-          break;
+          const uint4 v = read16(k, pos);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int i2 = 0; i2 < 4; ++i2) {
+              const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
+#pragma unroll
+              for (int i = 0; i < P; ++i) {
+                if ((lr >> i) & 1u) {
+                  if (st[i] != kEmpty) {
+                    const uint32_t s2 = tab.next(st[i], c);
+                    st[i] = (s2 == dead) ? kEmpty : s2;
+                  }
+                }
+              }
+            }
+            // merge lanes whose candidates met (within each register)
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              if ((lr >> i) & 1u) {
+                const unsigned grp = __match_any_sync(kFull, st[i]);
+                if (st[i] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[i] = kEmpty;
+              }
+            }
+          }
+          pos += 16;
+          uint32_t total = 0, nlr = 0;
+          unsigned bl[P];
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            bl[i] = ((lr >> i) & 1u) ? __ballot_sync(kFull, st[i] != kEmpty) : 0u;
+            total += __popc(bl[i]);
+            if (bl[i]) nlr |= 1u << i;
+          }
+          lr = nlr;
+          if (total <= 32 && (lr & ~1u)) {
+            // all survivors fit one register: compact them into register 0, then merge
+            uint32_t base = 0;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              if (st[i] != kEmpty) cbuf[base + __popc(bl[i] & lt_mask)] = st[i];
+              base += __popc(bl[i]);
+            }
+            __syncwarp();
+            st[0] = lane < total ? cbuf[lane] : kEmpty;
+#pragma unroll
+            for (int i = 1; i < P; ++i) st[i] = kEmpty;
+            __syncwarp();
+            const unsigned grp = __match_any_sync(kFull, st[0]);
+            if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
+            bl[0] = __ballot_sync(kFull, st[0] != kEmpty);
+#pragma unroll
+            for (int i = 1; i < P; ++i) bl[i] = 0;
+            total = __popc(bl[0]);
+            lr = 1;
+          }
+          if (total <= 1) {
+            outcome = 1;
+            if (total == 0) {
+              sigma = dead;
+            } else {
+              uint32_t reg = 0, holder = 0;
+#pragma unroll
+              for (int i = P - 1; i >= 0; --i)
+                if (bl[i]) {
+                  reg = (uint32_t)i;
+                  holder = __ffs(bl[i]) - 1;
+                }
+              uint32_t val = kEmpty;
+#pragma unroll
+              for (int i = 0; i < P; ++i)
+                if ((uint32_t)i == reg) val = st[i];
+              sigma = __shfl_sync(kFull, val, holder);
+            }
+            break;
+          }
+          if (total <= kLaneCand && lr == 1u) {
+            // few survivors left: the lane that owns the row finishes them (phase 2b)
+            if (st[0] != kEmpty) hand[k * kLaneCand + __popc(bl[0] & lt_mask)] = (uint16_t)st[0];
+            sigma = total;
+            outcome = 2;
+            break;
+          }
+        }
+        if (lane == k) {
+          my_conv = outcome == 1;
+          my_t = outcome == 3 ? (uint32_t)p.S : pos;
+          my_sigma = outcome == 1 ? sigma : kEmpty;
+          my_hand = outcome == 2 ? sigma : 0u;
         }
       }
-      if (lane == k) {
-        my_conv = conv;
-        my_t = conv ? pos : (uint32_t)p.S;
-        my_sigma = sigma;
+
+      // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
+      if (__ballot_sync(kFull, my_hand != 0) && !failed) {
+        __syncwarp();
+        if (my_hand) {
+          uint32_t ls[kLaneCand];
+#pragma unroll
+          for (uint32_t i = 0; i < kLaneCand; ++i)
+            ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
+          uint32_t L = my_hand, pos = my_t;
+          for (;;) {
+            if (pos >= cap) {
+              my_conv = 0;
+              my_t = (uint32_t)p.S;
+              break;
+            }
+            const uint4 v = read16(lane, pos);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const uint32_t c = tab.col(byte_of(v, q));
+#pragma unroll
+              for (uint32_t i = 0; i < kLaneCand; ++i) {
+                if (i < L && ls[i] != kEmpty) {
+                  const uint32_t s2 = tab.next(ls[i], c);
+                  ls[i] = (s2 == dead) ? kEmpty : s2;
+                }
+              }
+            }
+            pos += 16;
+#pragma unroll
+            for (uint32_t i = 0; i < kLaneCand; ++i)
+#pragma unroll
+              for (uint32_t jj = i + 1; jj < kLaneCand; ++jj)
+                if (ls[jj] == ls[i]) ls[jj] = kEmpty;
+            uint32_t out[kLaneCand];
+#pragma unroll
+            for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
+            uint32_t np = 0;
+#pragma unroll
+            for (uint32_t i = 0; i < kLaneCand; ++i) {
+              const bool keep = ls[i] != kEmpty;
+#pragma unroll
+              for (uint32_t qq = 0; qq < kLaneCand; ++qq)
+                if (keep && qq == np) out[qq] = ls[i];
+              np += keep ? 1u : 0u;
+            }
+#pragma unroll
+            for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
+            L = np;
+            if (L <= 1) {
+              my_conv = 1;
+              my_t = pos;
+              my_sigma = L ? ls[0] : dead;
+              break;
+            }
+          }
+          my_hand = 0;
+        }
+        __syncwarp();
       }
     }
 
@@ -390,7 +582,7 @@ __global__ void __launch_bounds__(1024, 1)
       const uint32_t k = __ffs(nonconv) - 1;
       nonconv &= nonconv - 1;
       const uint64_t r = row0 + k;
-      const uint32_t cls = p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
+      const uint32_t cls = cand_class(r);
       const uint32_t off = D.img_off[cls];
       const uint32_t m = D.img_off[cls + 1] - off;
       for (uint32_t base = 0; base < m; base += 32) {
@@ -406,8 +598,9 @@ __global__ void __launch_bounds__(1024, 1)
       }
     }
 
-    // 4. main run: each lane runs its merged state over the rest of its row from smem
-    uint32_t s = my_sigma, mu = 0;
+    // 4. main run: each lane runs its merged state over the rest of its row from smem,
+    //    remembering the first and last 16-byte vectors that contain matches
+    uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0;
     const bool run = active && my_conv;
     for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
       const uint32_t b = blk % kStages;
@@ -423,7 +616,7 @@ __global__ void __launch_bounds__(1024, 1)
       const uint8_t* stg = sm + stage0 + b * kStageBytes + lane * kBox;
 #pragma unroll
       for (uint32_t i = 0; i < kBox / 16; ++i)
-        v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ (lane & 7u)) * 16u));
+        v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane >> 1) & 3u)) * 16u));
       __syncwarp();
       if (blk + kStages < nblk) {
         if (lane == 0) {
@@ -438,18 +631,45 @@ __global__ void __launch_bounds__(1024, 1)
         const uint32_t col0 = blk * kBox;
 #pragma unroll
         for (uint32_t i = 0; i < kBox / 16; ++i) {
-          if (col0 + i * 16u >= my_t) {
+          const uint32_t col = col0 + i * 16u;
+          if (col >= my_t) {
+            const uint32_t mu0 = mu, s0 = s;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               s = tab.next(s, tab.col(byte_of(v[i], q)));
               mu += (s >= A);
+            }
+            if (mu != mu0) {
+              if (fv == kEmpty) {
+                fv = col;
+                fs = s0;
+              }
+              lvv = col;
+              ls = s0;
             }
           }
         }
       }
     }
     if (failed) continue;
-    if (run && myrow == p.R - 1 && p.tail) s = run_bytes(tab, body + p.R * p.S, p.tail, s, dead, A, &mu);
+    lv = (fv == kEmpty) ? 0u : lvv + 16u;
+    if (run && last_row && p.tail) {
+      const uint8_t* tp = body + p.R * p.S;
+      for (uint64_t o = 0; o < p.tail; ++o) {
+        const uint32_t s0 = s;
+        s = tab.next(s, tab.col(ldg8(tp + o)));
+        if (s >= A) {
+          ++mu;
+          if (fv == kEmpty) {
+            fv = (uint32_t)(p.S + o);
+            fs = s0;
+          }
+          lvv = (uint32_t)(p.S + o);
+          ls = s0;
+          lv = lvv + 1;
+        }
+      }
+    }
     const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
 
     // 5. the chunk's end state is known now if every row merged
@@ -460,19 +680,20 @@ __global__ void __launch_bounds__(1024, 1)
 
     // rows k >= 1: start = end of row k-1 (fast path), count the merged prefix [0, t)
     uint32_t x_k = __shfl_up_sync(kFull, E, 1);
-    uint32_t cnt_k = 0, dies_k = 0;
+    uint32_t cnt_k = 0, dies_k = 0, pre_k = 0, died_pre = 0;
     if (fast && active && lane >= 1) {
       if (x_k == dead) {
         dies_k = 1;
+        died_pre = 1;
       } else {
-        uint32_t pre = 0;
-        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre);
+        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre_k);
         if (y == dead) {
           dies_k = 1;
-          cnt_k = pre;
+          died_pre = 1;
+          cnt_k = pre_k;
         } else {
           if (y != my_sigma) set_error(p.result, kErrInternal);
-          cnt_k = pre + mu;
+          cnt_k = pre_k + mu;
           dies_k = (E == dead);
         }
       }
@@ -508,20 +729,22 @@ __global__ void __launch_bounds__(1024, 1)
       if (lane == 0) {
         x_k = s_j;
         if (j == 0) {
+          pre_k = 0;
           cnt_k = head_cnt + mu;
           dies_k = (E == dead);
         } else if (s_j == dead) {
           dies_k = 1;
+          died_pre = 1;
           cnt_k = 0;
         } else {
-          uint32_t pre = 0;
-          const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre);
+          const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre_k);
           if (y == dead) {
             dies_k = 1;
-            cnt_k = pre;
+            died_pre = 1;
+            cnt_k = pre_k;
           } else {
             if (y != my_sigma) set_error(p.result, kErrInternal);
-            cnt_k = pre + mu;
+            cnt_k = pre_k + mu;
             dies_k = (E == dead);
           }
         }
@@ -536,19 +759,19 @@ __global__ void __launch_bounds__(1024, 1)
         const uint32_t muk = __shfl_sync(kFull, mu, k);
         const uint32_t ck = __shfl_sync(kFull, my_conv, k);
         const uint32_t hk = __shfl_sync(kFull, head_cnt, k);
-        uint32_t cnt = 0, xin = x;
+        uint32_t cnt = 0, xin = x, pre = 0, dpre = 0;
         if (lane == 0) {
           const uint64_t r = row0 + k;
           if (x == dead) {
-            cnt = 0;
+            dpre = 1;
           } else if (r == 0) {
             cnt = hk + muk;
             x = Ek;
           } else if (ck) {
-            uint32_t pre = 0;
             const uint32_t y = run_range16(tab, body + r * p.S, tk, x, dead, A, &pre);
             if (y == dead) {
               cnt = pre;
+              dpre = 1;
               x = dead;
             } else {
               if (y != sk) set_error(p.result, kErrInternal);
@@ -556,8 +779,7 @@ __global__ void __launch_bounds__(1024, 1)
               x = Ek;
             }
           } else {
-            const uint32_t cls =
-                p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
+            const uint32_t cls = cand_class(r);
             const uint32_t slot = D.rank[(uint64_t)cls * D.n + x];
             if (slot == kNoSlot) {
               set_error(p.result, kErrInternal);
@@ -570,10 +792,14 @@ __global__ void __launch_bounds__(1024, 1)
         }
         xin = __shfl_sync(kFull, xin, 0);
         cnt = __shfl_sync(kFull, cnt, 0);
+        pre = __shfl_sync(kFull, pre, 0);
+        dpre = __shfl_sync(kFull, dpre, 0);
         x = __shfl_sync(kFull, x, 0);
         if (lane == k) {
           x_k = xin;
           cnt_k = cnt;
+          pre_k = pre;
+          died_pre = dpre;
           dies_k = (x == dead);
         }
       }
@@ -648,10 +874,10 @@ __global__ void __launch_bounds__(1024, 1)
     if (lane == 0 && !skip)
       st_release(&p.status[j], pack_status(kFlagInclusive, inc.dead, E_chunk, inc.count));
 
-    // 9. per-row records for the emit pass
+    // 9. per-row records for the emit pass: offset and the windows holding the matches
     if (p.segrec != nullptr) {
       const bool live_row = active && !ex.dead && lane <= first_dead;
-      uint64_t rc = live_row ? cnt_k : 0;
+      const uint64_t rc = live_row ? cnt_k : 0;
       uint64_t incl = rc;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -663,6 +889,31 @@ __global__ void __launch_bounds__(1024, 1)
         sr.x = live_row ? x_k : dead;
         sr.count = (uint32_t)rc;
         sr.offset = ex.count + incl - rc;
+        sr.flags = 0;
+        sr.pad[0] = sr.pad[1] = 0;
+        // default: replay the whole window [fv, lv) from fs (no fast replay)
+        sr.lvv = kEmpty;
+        sr.ls = 0;
+        if (!my_conv) {
+          sr.fv = 0;
+          sr.fs = x_k;
+          sr.lv = (uint32_t)rowlen;
+        } else if (myrow == 0 && head_cnt > 0) {
+          sr.flags = kHeadFlag;
+          sr.fs = x_k;
+          sr.fv = 0;
+          sr.lv = mu ? lv : 0u;
+        } else if (pre_k > 0) {
+          sr.fv = 0;
+          sr.fs = x_k;
+          sr.lv = (!died_pre && mu) ? lv : my_t;
+        } else {
+          sr.fv = fv == kEmpty ? 0u : fv;
+          sr.fs = fs;
+          sr.lv = lv;
+          sr.lvv = lvv;
+          sr.ls = ls;
+        }
         p.segrec[myrow] = sr;
       }
     }
@@ -685,64 +936,72 @@ __global__ void __launch_bounds__(1024, 1)
 }
 
 // ---------------------------------------------------------------------------------------
-// Emit pass: one thread per row with matches, re-run from the resolved start.
+// Emit pass: one thread per row with matches.  It first replays the first and the last
+// matching vectors; when that does not account for every match of the row, it replays the
+// whole window [fv, lv) instead.  Positions are written at the row's offset.
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE>
-__global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = smem_raw;
-  const DeviceDfa& D = p.dfa;
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
-    uint4* dst = reinterpret_cast<uint4*>(sm + p.smem_colmap_off);
-    for (uint32_t i = threadIdx.x; i < 1024 / 16; i += blockDim.x) dst[i] = src[i];
-    if (LAYOUT != kClassGlobal) {
-      const uint4* ts = reinterpret_cast<const uint4*>(D.table);
-      uint4* td = reinterpret_cast<uint4*>(sm + p.smem_table_off);
-      for (uint32_t i = threadIdx.x; i < D.table_bytes / 16; i += blockDim.x) td[i] = ts[i];
-    }
-  }
-  __syncthreads();
-  Tab<LAYOUT, ESIZE> tab;
-  tab.sm = sm;
-  tab.table_off = p.smem_table_off;
-  tab.colmap_off = p.smem_colmap_off;
-  tab.gtable = D.table;
-  tab.rowbytes = D.rowbytes;
-  const uint32_t A = D.first_accept;
-  const uint32_t dead = D.dead;
-  const uint8_t* body = p.text + p.h;
-  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
-       r += (uint64_t)gridDim.x * blockDim.x) {
-    const SegRec sr = p.segrec[r];
-    if (sr.count == 0 || sr.offset >= p.capacity) continue;
-    uint64_t o = sr.offset;
-    const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
-    uint32_t x = sr.x;
-    if (r == 0) {
-      for (uint64_t i = 0; i < p.h && o < end; ++i) {
-        x = tab.next(x, tab.col(ldg8(p.text + i)));
-        if (x >= A) p.positions[o++] = i;
-      }
-    }
-    const uint8_t* rowp = body + r * p.S;
-    const uint64_t gbase = p.h + r * p.S;
-    for (uint64_t off = 0; off < p.S && o < end; off += 16) {
+__device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p, uint64_t r,
+                                           uint32_t from, uint32_t to, uint32_t& x, uint64_t& o,
+                                           uint64_t end) {
+  const uint8_t* rowp = p.text + p.h + r * p.S;
+  const uint64_t gbase = p.h + r * p.S;
+  const uint32_t A = p.dfa.first_accept;
+  uint64_t off = from;
+  while (off < to && o < end) {
+    if ((off & 15u) == 0 && off + 16 <= p.S && off + 16 <= to) {
       const uint4 v = ldg16(rowp + off);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         x = tab.next(x, tab.col(byte_of(v, i)));
         if (x >= A && o < end) p.positions[o++] = gbase + off + (uint64_t)i;
       }
+      off += 16;
+    } else {
+      x = tab.next(x, tab.col(ldg8(rowp + off)));
+      if (x >= A) p.positions[o++] = gbase + off;
+      off += 1;
     }
-    if (r == p.R - 1) {
-      const uint64_t tb = p.h + p.R * p.S;
-      for (uint64_t i = 0; i < p.tail && o < end; ++i) {
-        x = tab.next(x, tab.col(ldg8(p.text + tb + i)));
-        if (x >= A) p.positions[o++] = tb + i;
+  }
+}
+
+template <int LAYOUT, int ESIZE>
+__global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const DeviceDfa& D = p.dfa;
+  load_tables<LAYOUT, ESIZE>(sm, D);
+  __syncthreads();
+  Tab<LAYOUT, ESIZE> tab;
+  tab.sm = sm;
+  tab.gtable = D.table;
+  tab.rowbytes = D.rowbytes;
+  const uint32_t A = D.first_accept;
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    const SegRec sr = p.segrec[r];
+    if (sr.count == 0 || sr.offset >= p.capacity) continue;
+    const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
+    uint64_t o = sr.offset;
+    uint32_t x = sr.fs;
+    if (sr.flags & kHeadFlag) {
+      for (uint64_t i = 0; i < p.h && o < end; ++i) {
+        x = tab.next(x, tab.col(ldg8(p.text + i)));
+        if (x >= A) p.positions[o++] = i;
       }
     }
-    (void)dead;
+    if (sr.lvv != kEmpty && sr.lvv > sr.fv) {
+      // fast replay: the first matching vector, then the last one
+      const uint32_t first_end = sr.fv + 16 <= sr.lvv ? sr.fv + 16 : sr.lvv;
+      emit_range(tab, p, r, sr.fv, first_end, x, o, end);
+      uint32_t y = sr.ls;
+      emit_range(tab, p, r, sr.lvv, sr.lv, y, o, end);
+      if (o == end) continue;
+      // matches lie between the two vectors: replay the whole window
+      o = sr.offset;
+      x = sr.fs;
+    }
+    emit_range(tab, p, r, sr.fv, sr.lv, x, o, end);
   }
 }
 
@@ -751,25 +1010,14 @@ __global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE>
 __global__ void k_tiny(const ScanParams p) {
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = smem_raw;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
   const DeviceDfa& D = p.dfa;
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
-    uint4* dst = reinterpret_cast<uint4*>(sm + p.smem_colmap_off);
-    for (uint32_t i = threadIdx.x; i < 1024 / 16; i += blockDim.x) dst[i] = src[i];
-    if (LAYOUT != kClassGlobal) {
-      const uint4* ts = reinterpret_cast<const uint4*>(D.table);
-      uint4* td = reinterpret_cast<uint4*>(sm + p.smem_table_off);
-      for (uint32_t i = threadIdx.x; i < D.table_bytes / 16; i += blockDim.x) td[i] = ts[i];
-    }
-  }
+  load_tables<LAYOUT, ESIZE>(sm, D);
   __syncthreads();
   if (threadIdx.x != 0) return;
   Tab<LAYOUT, ESIZE> tab;
   tab.sm = sm;
-  tab.table_off = p.smem_table_off;
-  tab.colmap_off = p.smem_colmap_off;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
   uint32_t x = p.init_state;

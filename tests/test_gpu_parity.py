@@ -198,3 +198,33 @@ def test_host_buffers(torch):
     got = pm.parem_match_host(load(GATTACA), text, pos)
     assert (got.final_state, got.match_count) == (want.final_state, want.match_count)
     assert np.array_equal(pos[:got.n_written], want.positions)
+
+
+@pytest.mark.parametrize("n_states,n_sym,layout", [(300, 140, 3), (300, 200, 4), (150, 4, 0), (700, 30, 1)])
+def test_table_layouts_and_register_counts(torch, n_states, n_sym, layout):
+    t, acc = wl.random_dfa(n_states, n_sym, max(1, n_states // 10), seed=n_states + n_sym)
+    spec = wl.DfaSpec(t, 0, acc, None, f"rand{n_states}x{n_sym}")
+    assert pm.parem_prepare_info(t, None, 0, acc).layout == layout
+    text = wl.uniform_text(150_000, n_sym, seed=n_sym)
+    check(torch, spec, text, offset=6, opts=pm.MatchOpts(segment_bytes=2048))
+    check(torch, spec, text[:40_000], opts=pm.MatchOpts(segment_bytes=128))
+
+
+@pytest.mark.parametrize("seg", [128, 640, 4096])
+def test_grouped_speculation_row_packing(torch, seg):
+    # candidate sets of 1..4 states (G = 4): eight rows speculated per warp pass
+    for spec in (GATTACA, PARALLEL):
+        text = wl.uniform_text(300_000 + 11, spec.n_symbols + 1, seed=seg)  # includes bytes outside Sigma
+        check(torch, spec, text, offset=seg % 16, opts=pm.MatchOpts(segment_bytes=seg))
+
+
+def test_emit_windows_with_sparse_and_clustered_matches(torch):
+    # rows with one match, two distant matches and many matches in between
+    kws = wl.random_keywords(8, 3, 6, seed=3)
+    sym = wl.letters_byte_map()
+    t, acc = wl.aho_corasick_dfa([[int(sym[b]) for b in kw] for kw in kws], 27)
+    spec = wl.DfaSpec(t, 0, acc, sym, "ac8")
+    text = wl.zipf_words_text(1 << 20, plant_rate=2e-3, keywords=kws)
+    text[300_000:300_400] = np.frombuffer((kws[0] + b" ") * 100, np.uint8)[:400]
+    check(torch, spec, text, offset=4, opts=pm.MatchOpts(segment_bytes=1024))
+    check(torch, spec, text, offset=0)
