@@ -55,6 +55,11 @@ extern "C" {
 #define PAREM_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define PAREM_ERR_INTERNAL (-6)    /* a device-side self-check failed */
 #define PAREM_ERR_UNSUPPORTED (-7) /* valid request outside what this build supports */
+#define PAREM_ERR_TOO_LARGE (-8)   /* parem_match_noalloc: the request needs more scratch than
+                                      its fixed area (PAREM_NOALLOC_SCRATCH_BYTES) holds */
+
+/* Size of the fixed device scratch area used by parem_match_noalloc (16 MiB). */
+#define PAREM_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 typedef struct parem_dfa parem_dfa; /* opaque; tables resident on one device */
 
@@ -188,6 +193,35 @@ int parem_match_ex(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint
  */
 int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                      uint64_t capacity, void* stream, parem_result* out);
+
+/*
+ * parem_match_noalloc -- parem_match for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for users of the library.  Some
+ * callers must not have a library call cudaMalloc behind their back: applications whose
+ * device memory is handed to their own pool allocator at start-up (so a library allocation
+ * fails, or fragments the pool they manage), and latency-sensitive code that cannot afford
+ * the implicit device-wide synchronisation that allocating and freeing device memory may
+ * cause.  parem_match keeps per-stream scratch that it allocates on first use and grows on
+ * demand; this variant runs the same kernels with all of their scratch (ticket counter,
+ * result word, chunk status words, per-row records and slot maps) in one fixed array of
+ * PAREM_NOALLOC_SCRATCH_BYTES in device memory, defined statically in the library.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *   Arguments, results and errors are those of parem_match, plus PAREM_ERR_TOO_LARGE when
+ *   the scan of this text would need more scratch than the fixed area holds: 8 bytes per
+ *   32-row chunk, 48 bytes per row when positions are requested, and 8 bytes per candidate
+ *   per row for the slot maps (with the default plan: about 500 MiB of text for an
+ *   Aho-Corasick DFA with 47 candidates per class, far more for small candidate sets).
+ *   Nothing is written to the outputs in that case.
+ *   Every GPU that loads the library holds the array until the process exits.  The first
+ *   call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ *   device current); make that first call before any stream capture begins.  All calls share
+ *   the one array: the library clears the parts that must start at zero on every call, but
+ *   calls whose work overlaps on the GPU (different streams, or host threads) race on it and
+ *   give wrong results; serialise them.
+ */
+int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
+                        uint64_t capacity, void* stream, parem_result* out);
 
 /* Plan and kernel times of the last scan issued on (current device, stream); waits for the
  * recorded events.  Errors: INVALID_ARG (no scan yet), CUDA. */

@@ -25,13 +25,16 @@ __all__ = [
     "PAREM_NONE", "PAREM_NONE16", "ParemError", "MatchResult", "DfaInfo", "Dfa", "MatchOpts",
     "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa",
     "parem_match", "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror",
-    "parem_version", "parem_last_stats", "Stats", "EXPORTED_SYMBOLS",
+    "parem_version", "parem_last_stats", "parem_match_noalloc", "Stats", "EXPORTED_SYMBOLS",
+    "PAREM_ERR_TOO_LARGE", "PAREM_NOALLOC_SCRATCH_BYTES",
 ]
 
 PAREM_NONE = 0xFFFFFFFF
 PAREM_NONE16 = 0xFFFF
 PAREM_OK = 0
 PAREM_ERR_CAPACITY = -3
+PAREM_ERR_TOO_LARGE = -8
+PAREM_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -40,7 +43,7 @@ _LIB = None
 EXPORTED_SYMBOLS = [
     "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
-    "parem_last_stats",
+    "parem_last_stats", "parem_match_noalloc",
 ]
 
 
@@ -137,13 +140,14 @@ def load_library(build_if_missing: bool = False):
     lib.parem_match.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
     lib.parem_match_ex.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(MatchOpts), vp, ctypes.POINTER(_Result)]
     lib.parem_match_host.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
+    lib.parem_match_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, ctypes.POINTER(_Result)]
     lib.parem_release_scratch.argtypes = [vp]
     lib.parem_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.parem_strerror.argtypes = [ctypes.c_int]
     lib.parem_strerror.restype = ctypes.c_char_p
     lib.parem_version.restype = ctypes.c_char_p
     for f in ("parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_match", "parem_match_ex",
-              "parem_match_host", "parem_release_scratch", "parem_last_stats"):
+              "parem_match_host", "parem_release_scratch", "parem_last_stats", "parem_match_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -306,3 +310,19 @@ def parem_last_stats(stream=None) -> dict:
     if rc != PAREM_OK:
         raise ParemError(rc, "parem_last_stats")
     return st.as_dict()
+
+
+def parem_match_noalloc(dfa: Dfa, text, positions=None, stream=None, length=None, capacity=None) -> MatchResult:
+    """parem_match with all scratch in the library's fixed device array (no allocation).
+
+    For callers that cannot let the library allocate device memory.  Raises ParemError with
+    status PAREM_ERR_TOO_LARGE when the text needs more scratch than the fixed area holds.
+    Calls share the area, so calls that overlap on the GPU must be serialised by the caller.
+    """
+    lib = load_library()
+    tp, n = _ptr_len(text, length)
+    pp, pbytes = _ptr_len(positions)
+    cap = (pbytes // 8 if capacity is None else int(capacity)) if pp else 0
+    res = _Result()
+    rc = lib.parem_match_noalloc(dfa.handle, tp, n, pp, cap, _stream(stream), ctypes.byref(res))
+    return _finish(rc, res, "parem_match_noalloc")

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libparem.so")
-SOURCES = ["parem_api.cu", "parem_prep.cpp", "parem_k_byte.cu", "parem_k_class.cu", "parem_k_global.cu"]
+SOURCES = ["parem_api.cu", "parem_prep.cpp", "parem_k_byte.cu", "parem_k_class.cu", "parem_k_global.cu",
+           "parem_noalloc.cu"]
 HEADERS = ["parem_internal.h", "parem_launch.h", "parem_scan.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -19,14 +19,6 @@
 
 using namespace parem;
 
-struct parem_dfa {
-  int device = 0;
-  Prepared host;
-  DeviceDfa dev{};
-  void* dmem = nullptr;
-  parem_dfa_info info{};
-};
-
 namespace {
 
 constexpr uint32_t kSmemTableBudget = 96 * 1024;
@@ -160,6 +152,7 @@ extern "C" const char* parem_strerror(int status) {
     case PAREM_ERR_CUDA: return "CUDA runtime error";
     case PAREM_ERR_INTERNAL: return "device-side self-check failed";
     case PAREM_ERR_UNSUPPORTED: return "unsupported request";
+    case PAREM_ERR_TOO_LARGE: return "the request needs more scratch than the fixed area of parem_match_noalloc";
     default: return "unknown status";
   }
 }

@@ -6,7 +6,16 @@
 
 #include "parem_internal.h"
 
-struct parem_dfa;
+#include "../../include/parem.h"
+
+// A loaded DFA: the host preparation and its device copy (opaque in the C ABI).
+struct parem_dfa {
+  int device = 0;
+  parem::Prepared host;
+  parem::DeviceDfa dev{};
+  void* dmem = nullptr;
+  parem_dfa_info info{};
+};
 
 namespace parem {
 
@@ -21,6 +30,9 @@ struct Plan {
   uint64_t h, S, R, tail, n_chunks;
   uint32_t spec_cap;
 };
+
+// The launch plan of one scan (parem_api.cu).
+int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const parem_match_opts* o, Plan* pl);
 
 cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, const CUtensorMap& tm,
                                  const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);

@@ -1,0 +1,76 @@
+"""parem_match_noalloc: the scan for callers that cannot allocate device memory.
+
+Some callers cannot let a library call cudaMalloc: their device memory is handed to their
+own pool allocator at start-up, or allocation (and the synchronisation it may imply) is not
+allowed on their path.  parem_match_noalloc runs the same kernels as parem_match with all
+scratch in a fixed device array inside the library.  These checks compare it with
+parem_match through the C ABI, bit for bit, on two calls in a row (the array keeps the last
+call's contents, so the second call checks that what must start at zero is cleared), and
+check the clear error for a request that needs more scratch than the array holds.
+
+The file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+import paper_1412_1741_gb300 as pm
+from paper_1412_1741_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+
+    from paper_1412_1741_gb300 import build
+
+    build.build()
+    pm.load_library()
+    assert _t.cuda.is_available()
+    return _t
+
+
+def _cases():
+    g = wl.gattaca_dfa()
+    a = wl.keywords_ac_dfa()
+    return [
+        (g, wl.uniform_text(1 << 20, 4, seed=0), 0),
+        (g, wl.uniform_text(300_001, 5, seed=1), 3),  # bytes outside the alphabet, unaligned
+        (a, wl.zipf_words_text(8 << 20, plant_rate=1e-4, keywords=a.meta["keywords"]), 7),
+    ]
+
+
+def test_noalloc_matches_parem_match_on_two_calls_in_a_row(torch):
+    for spec, text, offset in _cases():
+        dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+        buf = torch.zeros(text.size + offset + 16, dtype=torch.uint8, device="cuda")
+        view = buf[offset:offset + text.size]
+        view.copy_(torch.from_numpy(np.array(text)))
+        ref = pm.parem_match(dfa, view)
+        cap = max(1, ref.match_count)
+        ref_pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+        ref = pm.parem_match(dfa, view, ref_pos)
+        for _ in range(2):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            got = pm.parem_match_noalloc(dfa, view, pos)
+            torch.cuda.synchronize()
+            assert (got.final_state, got.accepted, got.match_count, got.n_written) == \
+                   (ref.final_state, ref.accepted, ref.match_count, ref.n_written)
+            assert torch.equal(pos, ref_pos)
+            cnt = pm.parem_match_noalloc(dfa, view)  # count only
+            assert (cnt.final_state, cnt.match_count) == (ref.final_state, ref.match_count)
+        dfa.free()
+
+
+def test_noalloc_rejects_requests_beyond_the_fixed_area(torch):
+    # 5000 states over 4 symbols: ~3160 candidates per class, so the slot maps of a 64 MiB
+    # text need far more than the 16 MiB area
+    t, acc = wl.random_dfa(5000, 4, 500, seed=5)
+    dfa = pm.parem_load_dfa(t, None, 0, acc)
+    text = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pm.ParemError) as e:
+        pm.parem_match_noalloc(dfa, text)
+    assert e.value.status == pm.PAREM_ERR_TOO_LARGE
+    assert "fixed area" in pm.parem_strerror(pm.PAREM_ERR_TOO_LARGE)
+    dfa.free()
