@@ -125,6 +125,8 @@ typedef struct {
   uint32_t candidate_regs;  /* candidate registers per lane in the speculation (1 or 8) */
   uint32_t spec_cap_bytes;  /* longest speculative prefix per segment */
   uint32_t kernels;         /* kernels launched by the call */
+  uint32_t emit_replays;    /* rows whose positions the emit pass replayed (not recorded in pass 1) */
+  uint32_t emit_max_window; /* longest window (bytes) the emit pass replayed */
   uint32_t reserved;
 } parem_stats;
 
@@ -209,8 +211,8 @@ int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, ui
  * no cudaMalloc, cudaFree or other allocating routine.
  *   Arguments, results and errors are those of parem_match, plus PAREM_ERR_TOO_LARGE when
  *   the scan of this text would need more scratch than the fixed area holds: 8 bytes per
- *   32-row chunk, 48 bytes per row when positions are requested, and 8 bytes per candidate
- *   per row for the slot maps (with the default plan: about 500 MiB of text for an
+ *   32-row chunk, 112 bytes per row when positions are requested, and 8 bytes per candidate
+ *   per row for the slot maps (with the default plan: about 400 MiB of text for an
  *   Aho-Corasick DFA with 47 candidates per class, far more for small candidate sets).
  *   Nothing is written to the outputs in that case.
  *   Every GPU that loads the library holds the array until the process exits.  The first

@@ -85,7 +85,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("scan_ms", ctypes.c_float), ("emit_ms", ctypes.c_float), ("segment_bytes", ctypes.c_uint64),
                 ("rows", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("blocks", ctypes.c_uint32),
                 ("warps_per_block", ctypes.c_uint32), ("candidate_regs", ctypes.c_uint32),
-                ("spec_cap_bytes", ctypes.c_uint32), ("kernels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("spec_cap_bytes", ctypes.c_uint32), ("kernels", ctypes.c_uint32),
+                ("emit_replays", ctypes.c_uint32), ("emit_max_window", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

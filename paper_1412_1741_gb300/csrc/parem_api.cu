@@ -396,7 +396,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const bool emit = positions != nullptr && capacity > 0;
   const uint64_t o_status = 512;
   const uint64_t o_segrec = round_up(o_status + pl.n_chunks * 8, 256);
-  const uint64_t o_slot = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
+  const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
+  const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.R * (uint64_t)pl.cand_stride * 4;
   const uint64_t total = round_up(o_slot + 2 * slot_bytes, 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
@@ -427,6 +428,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.result = reinterpret_cast<DevResult*>(sb + 256);
   p.status = reinterpret_cast<unsigned long long*>(sb + o_status);
   p.segrec = emit ? reinterpret_cast<SegRec*>(sb + o_segrec) : nullptr;
+  p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
   p.positions = emit ? positions : nullptr;
@@ -472,6 +474,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   PAREM_CUDA_TRY(cudaMemcpyAsync(sc->host_res, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, stream));
   PAREM_CUDA_TRY(cudaStreamSynchronize(stream));
   const DevResult r = *sc->host_res;
+  sc->stats.emit_replays = r.emit_replays;
+  sc->stats.emit_max_window = r.emit_max_window;
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
   const uint32_t fs = r.final_state;

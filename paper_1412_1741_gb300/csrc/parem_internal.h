@@ -20,6 +20,9 @@ constexpr uint32_t kLaneCand = 8;        // survivors a lane takes over from the
 // followed by a 32-word compaction buffer
 constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4;
 constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
+constexpr uint32_t kSlotsFlag = 2u;      // SegRec.flags: every main-run match of the row is in its slots
+constexpr uint32_t kPreFlag = 4u;        // SegRec.flags: replay the merged prefix [0, t) from x
+constexpr uint32_t kRowSlots = 16;       // match positions pass 1 records per row
 constexpr uint64_t kMaxText = 1ull << 45;
 
 // Table layouts (parem_dfa_info.layout).  The class layouts read a 256-entry byte -> column
@@ -83,21 +86,27 @@ struct DeviceDfa {
 // Per-segment record for the emit pass: the matches of the row lie in the row-relative
 // window [fv, lv), which the emit pass re-runs from state fs.
 struct SegRec {
-  uint32_t fs;      // state at row offset fv (or, with kHeadFlag, the start before the head)
+  uint32_t fs;      // state at row offset fv, where the main-run window starts
   uint32_t count;   // matches inside the segment
   uint64_t offset;  // index of the segment's first match in the global position order
-  uint32_t fv, lv;  // window (row-relative bytes; the last row extends into the tail)
+  uint32_t fv, lv;  // main-run window (row-relative bytes; the last row extends into the tail)
   uint32_t lvv, ls; // last matching vector [lvv, lv) and the state at lvv (fast replay)
-  uint32_t x;       // true start state of the row
-  uint32_t flags;
-  uint32_t pad[2];
+  uint32_t x;       // true start state of the row (before the head bytes for row 0)
+  uint32_t flags;   // kHeadFlag | kPreFlag | kSlotsFlag
+  uint32_t t;       // length of the merged prefix replayed from x (kPreFlag)
+  uint32_t pre;     // matches in the head and the merged prefix
 };
+
+// Scratch bytes per row for recorded match positions (row-relative u32).
+constexpr uint32_t kRowSlotBytes = kRowSlots * 4;
 
 // Result word filled on the device.
 struct DevResult {
   uint32_t final_state;  // compact
   uint32_t error;        // kErr* or 0
   uint64_t count;
+  uint32_t emit_replays;     // rows whose positions the emit pass had to replay
+  uint32_t emit_max_window;  // longest replayed window (bytes)
 };
 
 // Parameters of one plain scan (one text).
@@ -121,6 +130,7 @@ struct ScanParams {
   uint32_t* ticket;
   unsigned long long* status;
   SegRec* segrec;          // nullptr when positions are not requested
+  uint32_t* slots;         // R * kRowSlots row-relative match positions (with segrec)
   uint32_t* slot_end;      // R * cand_stride
   uint32_t* slot_cnt;      // R * cand_stride
   DevResult* result;

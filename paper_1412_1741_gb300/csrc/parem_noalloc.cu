@@ -94,7 +94,8 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   const bool emit = positions != nullptr && capacity > 0;
   const uint64_t o_status = 512;
   const uint64_t o_segrec = up256(o_status + pl.n_chunks * 8);
-  const uint64_t o_slot = up256(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0));
+  const uint64_t o_rows = up256(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0));
+  const uint64_t o_slot = up256(o_rows + (emit ? pl.R * kRowSlotBytes : 0));
   const uint64_t slot_bytes = pl.R * (uint64_t)pl.cand_stride * 4;
   const uint64_t total = up256(o_slot + 2 * slot_bytes);
   if (total > PAREM_NOALLOC_SCRATCH_BYTES) return PAREM_ERR_TOO_LARGE;
@@ -124,6 +125,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   p.result = reinterpret_cast<DevResult*>(sb + 256);
   p.status = reinterpret_cast<unsigned long long*>(sb + o_status);
   p.segrec = emit ? reinterpret_cast<SegRec*>(sb + o_segrec) : nullptr;
+  p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
   p.positions = emit ? positions : nullptr;

@@ -600,8 +600,9 @@ __global__ void __launch_bounds__(1024, 1)
 
     // 4. main run: each lane runs its merged state over the rest of its row from smem,
     //    remembering the first and last 16-byte vectors that contain matches
-    uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0;
+    uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
     const bool run = active && my_conv;
+    uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
     for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
       const uint32_t b = blk % kStages;
       const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
@@ -646,6 +647,18 @@ __global__ void __launch_bounds__(1024, 1)
               }
               lvv = col;
               ls = s0;
+              if (myslots != nullptr && nrec < kRowSlots) {
+                // replay this vector to record its match positions (rare for sparse matches)
+                uint32_t x = s0;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                  x = tab.next(x, tab.col(byte_of(v[i], q)));
+                  if (x >= A) {
+                    if (nrec < kRowSlots) myslots[nrec] = col + (uint32_t)q;
+                    ++nrec;
+                  }
+                }
+              }
             }
           }
         }
@@ -667,6 +680,8 @@ __global__ void __launch_bounds__(1024, 1)
           lvv = (uint32_t)(p.S + o);
           ls = s0;
           lv = lvv + 1;
+          if (myslots != nullptr && nrec < kRowSlots) myslots[nrec] = lvv;
+          ++nrec;
         }
       }
     }
@@ -890,29 +905,33 @@ __global__ void __launch_bounds__(1024, 1)
         sr.count = (uint32_t)rc;
         sr.offset = ex.count + incl - rc;
         sr.flags = 0;
-        sr.pad[0] = sr.pad[1] = 0;
-        // default: replay the whole window [fv, lv) from fs (no fast replay)
+        sr.t = 0;
+        sr.pre = 0;
         sr.lvv = kEmpty;
         sr.ls = 0;
         if (!my_conv) {
+          // slot-map row: no merged run, replay the whole row from its start
           sr.fv = 0;
           sr.fs = x_k;
           sr.lv = (uint32_t)rowlen;
-        } else if (myrow == 0 && head_cnt > 0) {
-          sr.flags = kHeadFlag;
-          sr.fs = x_k;
-          sr.fv = 0;
-          sr.lv = mu ? lv : 0u;
-        } else if (pre_k > 0) {
-          sr.fv = 0;
-          sr.fs = x_k;
-          sr.lv = (!died_pre && mu) ? lv : my_t;
         } else {
-          sr.fv = fv == kEmpty ? 0u : fv;
+          if (myrow == 0 && head_cnt > 0) {
+            sr.flags |= kHeadFlag;
+            sr.pre = head_cnt;
+          } else if (pre_k > 0) {
+            sr.flags |= kPreFlag;
+            sr.t = my_t;
+            sr.pre = pre_k;
+          }
+          // main-run window (empty when the run died inside the prefix)
+          const bool main_live = !died_pre && mu > 0;
+          sr.fv = (main_live && fv != kEmpty) ? fv : 0u;
           sr.fs = fs;
-          sr.lv = lv;
-          sr.lvv = lvv;
+          sr.lv = main_live ? lv : 0u;
+          sr.lvv = main_live ? lvv : kEmpty;
           sr.ls = ls;
+          // every main-run match was recorded by pass 1: the emit pass only copies them
+          if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
         }
         p.segrec[myrow] = sr;
       }
@@ -948,6 +967,20 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
   const uint64_t gbase = p.h + r * p.S;
   const uint32_t A = p.dfa.first_accept;
   uint64_t off = from;
+  // aligned whole vectors inside the row, with the next vector's load in flight
+  if ((off & 15u) == 0 && off + 16 <= p.S && off + 16 <= to) {
+    uint4 nxt = ldg16(rowp + off);
+    while (off + 16 <= p.S && off + 16 <= to && o < end) {
+      const uint4 v = nxt;
+      if (off + 32 <= p.S && off + 32 <= to) nxt = ldg16(rowp + off + 16);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        x = tab.next(x, tab.col(byte_of(v, i)));
+        if (x >= A && o < end) p.positions[o++] = gbase + off + (uint64_t)i;
+      }
+      off += 16;
+    }
+  }
   while (off < to && o < end) {
     if ((off & 15u) == 0 && off + 16 <= p.S && off + 16 <= to) {
       const uint4 v = ldg16(rowp + off);
@@ -983,13 +1016,30 @@ __global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
     if (sr.count == 0 || sr.offset >= p.capacity) continue;
     const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
     uint64_t o = sr.offset;
-    uint32_t x = sr.fs;
     if (sr.flags & kHeadFlag) {
+      // row 0: the unaligned head bytes before the first full row
+      uint32_t x = sr.x;
       for (uint64_t i = 0; i < p.h && o < end; ++i) {
         x = tab.next(x, tab.col(ldg8(p.text + i)));
         if (x >= A) p.positions[o++] = i;
       }
+    } else if (sr.flags & kPreFlag) {
+      // matches inside the merged prefix [0, t), replayed from the row's true start
+      uint32_t x = sr.x;
+      emit_range(tab, p, r, 0u, sr.t, x, o, end);
     }
+    if (o >= end || sr.lv == 0) continue;
+    if (sr.flags & kSlotsFlag) {
+      // pass 1 recorded every main-run match of this row
+      const uint64_t gbase = p.h + r * p.S;
+      const uint32_t* sl = p.slots + r * kRowSlots;
+      for (uint32_t i = 0; o < end; ++i) p.positions[o++] = gbase + sl[i];
+      continue;
+    }
+    atomicAdd(&p.result->emit_replays, 1u);
+    atomicMax(&p.result->emit_max_window, sr.lv - sr.fv);
+    const uint64_t o_main = o;
+    uint32_t x = sr.fs;
     if (sr.lvv != kEmpty && sr.lvv > sr.fv) {
       // fast replay: the first matching vector, then the last one
       const uint32_t first_end = sr.fv + 16 <= sr.lvv ? sr.fv + 16 : sr.lvv;
@@ -998,7 +1048,7 @@ __global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
       emit_range(tab, p, r, sr.lvv, sr.lv, y, o, end);
       if (o == end) continue;
       // matches lie between the two vectors: replay the whole window
-      o = sr.offset;
+      o = o_main;
       x = sr.fs;
     }
     emit_range(tab, p, r, sr.fv, sr.lv, x, o, end);
