@@ -332,9 +332,13 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   const uint32_t table_smem = (P.layout == kClassGlobal || P.layout == kClassGlobalW) ? 0 : P.table_bytes;
   pl->table_smem = table_smem;
   const uint32_t fixed = kTableOff + table_smem + 1024;
-  const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + kSpecBytes;
+  // candidate sets larger than the registers run through a per-warp bitmap of the states
+  pl->bitmap_words = 0;
+  if (pl->P > 1 && m_need > 32u * pl->P && P.n <= 16384) pl->bitmap_words = (P.n + 31) / 32;
+  pl->spec_bytes = kSpecBytes + (pl->bitmap_words ? (uint32_t)round_up(8ull * pl->bitmap_words, 16) + 512u : 0u);
+  const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + pl->spec_bytes;
   int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
-  warps = std::min(warps, 32);
+  warps = std::min(warps, pl->P >= 4 ? 24 : 32);  // the launch bounds of the kernel variants
   if (o && o->warps_per_block) warps = std::min<int>(warps, (int)o->warps_per_block);
   if (warps < 1) return PAREM_ERR_UNSUPPORTED;
   pl->warps = warps;
@@ -417,6 +421,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.n_chunks = pl.n_chunks;
   p.init_state = init;
   p.group = pl.group;
+  p.bitmap_words = pl.bitmap_words;
+  p.spec_bytes = pl.spec_bytes;
   p.smem_table_bytes = pl.table_smem;
   p.enum_all = pl.enum_all;
   p.spec_cap = pl.spec_cap;

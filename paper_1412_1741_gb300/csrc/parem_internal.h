@@ -121,6 +121,8 @@ struct ScanParams {
   uint64_t n_chunks;       // ceil(R / 32)
   uint32_t init_state;     // compact start state (q0 or carried in)
   uint32_t group;          // lanes per row in the speculation when P == 1 (power of two <= 32)
+  uint32_t bitmap_words;   // words of the per-warp candidate bitmap (0: no bitmap phase)
+  uint32_t spec_bytes;     // per-warp speculation scratch in shared memory
   uint32_t enum_all;       // candidates = all live states
   uint32_t spec_cap;       // bytes of speculation before a segment counts as non-converged
   uint32_t cand_stride;    // slots per segment in the slot map

@@ -24,6 +24,8 @@ struct Plan {
   uint32_t enum_all;
   uint32_t cand_stride;
   uint32_t group;        // lanes per row in the grouped speculation (P == 1)
+  uint32_t bitmap_words; // per-warp candidate bitmap words (P > 1 and candidate sets > 32 * P)
+  uint32_t spec_bytes;   // per-warp speculation scratch
   int warps, grid;
   uint32_t table_smem;   // table bytes staged in shared memory (0 for the global layouts)
   size_t smem;

@@ -115,6 +115,8 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   p.n_chunks = pl.n_chunks;
   p.init_state = P.start;
   p.group = pl.group;
+  p.bitmap_words = pl.bitmap_words;
+  p.spec_bytes = pl.spec_bytes;
   p.smem_table_bytes = pl.table_smem;
   p.enum_all = 0;
   p.spec_cap = pl.spec_cap;

@@ -231,7 +231,7 @@ __device__ __forceinline__ uint32_t stage_region_off(const uint8_t* smem_raw, ui
 // is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE, int P>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
     k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
@@ -241,9 +241,11 @@ __global__ void __launch_bounds__(1024, 1)
   const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
   const uint32_t stage0 = region + warp * (kStages * kStageBytes);
   const uint32_t bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
-  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * kSpecBytes;
+  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * p.spec_bytes;
   uint16_t* hand = reinterpret_cast<uint16_t*>(sm + spec0);
   uint32_t* cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
+  // 2 x bitmap_words words of candidate bitmaps, then a list of up to 256 states
+  uint32_t* bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
   if (lane == 0) {
     for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + bar0 + 8 * s), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -400,9 +402,10 @@ __global__ void __launch_bounds__(1024, 1)
         const uint32_t cls = cand_class(r);
         const uint32_t off = D.img_off[cls];
         const uint32_t m = D.img_off[cls + 1] - off;
-        if (m <= 1 || m > 32u * P) {
+        const bool big = m > 32u * P;
+        if (m <= 1 || (big && p.bitmap_words == 0)) {
           if (lane == k) {
-            my_t = m > 32u * P ? (uint32_t)p.S : 0u;
+            my_t = big ? (uint32_t)p.S : 0u;
             my_conv = m <= 1;
             my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
           }
@@ -410,14 +413,105 @@ __global__ void __launch_bounds__(1024, 1)
         }
         uint32_t st[P];
         uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          const uint32_t slot = (uint32_t)i * 32u + lane;
-          st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
-          if ((uint32_t)i * 32u < m) lr |= 1u << i;
-        }
         uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
-        for (;;) {
+        if (big) {
+          // More candidates than registers: the warp keeps the candidate set as a bitmap over
+          // the states (duplicates merge by construction) until it fits 32 * P registers.
+          const uint32_t W = p.bitmap_words;
+          uint32_t* bm0 = bitmaps;
+          uint32_t* bm1 = bitmaps + W;
+          for (uint32_t w = lane; w < W; w += 32) bm0[w] = 0;
+          __syncwarp();
+          for (uint32_t slot = lane; slot < m; slot += 32) {
+            const uint32_t q = D.img[off + slot];
+            atomicOr(&bm0[q >> 5], 1u << (q & 31u));
+          }
+          __syncwarp();
+          uint32_t cnt = m;
+          for (;;) {
+            if (pos >= cap) {
+              outcome = 3;
+              break;
+            }
+            const uint4 v = read16(k, pos);
+#pragma unroll 1
+            for (int q = 0; q < 16; ++q) {
+              const uint32_t c = tab.col(byte_of(v, q));
+              for (uint32_t w = lane; w < W; w += 32) bm1[w] = 0;
+              __syncwarp();
+              for (uint32_t w = lane; w < W; w += 32) {
+                uint32_t bits = bm0[w];
+                while (bits) {
+                  // up to four independent lookups in flight
+                  uint32_t qs[4], nq[4];
+                  int nb = 0;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) {
+                    qs[u] = kEmpty;
+                    if (bits) {
+                      qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
+                      bits &= bits - 1;
+                      ++nb;
+                    }
+                  }
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) nq[u] = qs[u] != kEmpty ? tab.next(qs[u], c) : dead;
+#pragma unroll
+                  for (int u = 0; u < 4; ++u)
+                    if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
+                  (void)nb;
+                }
+              }
+              __syncwarp();
+              uint32_t* tmp = bm0;
+              bm0 = bm1;
+              bm1 = tmp;
+            }
+            pos += 16;
+            uint32_t local = 0;
+            for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+            cnt = __reduce_add_sync(kFull, local);
+            if (cnt <= 32u * P) break;
+          }
+          if (outcome == 0) {
+            // list the surviving states in the hand-over buffer, then load the registers
+            uint32_t local = 0;
+            for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+            uint32_t incl = local;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const uint32_t o = __shfl_up_sync(kFull, incl, d);
+              if (lane >= (uint32_t)d) incl += o;
+            }
+            uint32_t idx = incl - local;
+            // the list has its own buffer after the two bitmaps: the hand-over lists of
+            // earlier rows of this chunk must survive until phase 2b
+            uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
+            for (uint32_t w = lane; w < W; w += 32) {
+              uint32_t bits = bm0[w];
+              while (bits) {
+                list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
+                bits &= bits - 1;
+              }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              const uint32_t slot = (uint32_t)i * 32u + lane;
+              st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
+              if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
+            }
+            __syncwarp();
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const uint32_t slot = (uint32_t)i * 32u + lane;
+            st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
+            if ((uint32_t)i * 32u < m) lr |= 1u << i;
+          }
+        }
+        for (; outcome == 0;) {
           if (pos >= cap) {
             outcome = 3;
             break;

@@ -228,3 +228,20 @@ def test_emit_windows_with_sparse_and_clustered_matches(torch):
     text[300_000:300_400] = np.frombuffer((kws[0] + b" ") * 100, np.uint8)[:400]
     check(torch, spec, text, offset=4, opts=pm.MatchOpts(segment_bytes=1024))
     check(torch, spec, text, offset=0)
+
+
+@pytest.mark.parametrize("n_states,n_sym,seg", [(4096, 256, 8192), (2000, 27, 2048), (600, 4, 1024)])
+def test_bitmap_phase_for_large_candidate_sets(torch, n_states, n_sym, seg):
+    # |img(c)| ~ 0.63 n > 256: candidates start as a per-warp bitmap, then move to registers
+    t, acc = wl.random_dfa(n_states, n_sym, n_states // 10, seed=n_states)
+    spec = wl.DfaSpec(t, 0, acc, None, f"rand{n_states}x{n_sym}")
+    assert pm.parem_prepare_info(t, None, 0, acc).max_candidates > 256
+    text = wl.uniform_text(400_000 + 3, n_sym, seed=9)
+    check(torch, spec, text, offset=5, opts=pm.MatchOpts(segment_bytes=seg))
+
+
+def test_enumeration_mode_with_bitmap(torch):
+    t, acc = wl.random_dfa(600, 8, 60, seed=33)
+    spec = wl.DfaSpec(t, 0, acc, None, "rand600x8")
+    text = wl.uniform_text(200_000, 8, seed=10)
+    check(torch, spec, text, opts=pm.MatchOpts(enumerate_all=1, segment_bytes=2048))
