@@ -7,7 +7,7 @@ of Zipf(1.1)-distributed words with keywords planted at rate 1e-5.  One step = o
 parem_match over the whole device-resident text: speculation, main run, look-back and the
 emission of every match position (two kernels).  value = text bytes / time (GB/s, 1e9).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config d2|d1|d3|d6]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--config d2|d1|d3|d4|d5|d6]
 
 Under torchrun every rank scans its own text (independent problems, weak scaling, no
 data-path collective); the timed region is bracketed by barriers and the max over ranks is
@@ -30,8 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "scanned GB/s on 1 GB300 (fraction of HBM peak); batched vs plain; p99 ms"
-KERNEL_SOURCES = ["paper_1412_1741_gb300/csrc/parem_scan.cuh", "paper_1412_1741_gb300/csrc/parem_api.cu",
-                  "paper_1412_1741_gb300/csrc/parem_prep.cpp"]
+# the device code of the plain scan: DRAM counters taken on it stay valid while these are unchanged
+KERNEL_SOURCES = ["paper_1412_1741_gb300/csrc/parem_scan.cuh", "paper_1412_1741_gb300/csrc/parem_internal.h",
+                  "paper_1412_1741_gb300/csrc/parem_k_byte.cu", "paper_1412_1741_gb300/csrc/parem_k_class.cu",
+                  "paper_1412_1741_gb300/csrc/parem_k_global.cu"]
 
 CONFIGS = {
     "d2": dict(workload="sparse DFA: Aho-Corasick of 64 random keywords (len 8-24) over a-z+space, "
@@ -42,6 +44,14 @@ CONFIGS = {
                n=8 << 30),
     "d6": dict(workload="paper-shaped: automaton of Table I ('parallel', 9 states, 5 symbols), "
                         "2^30 uniform symbols", n=1 << 30),
+    "d4": dict(workload="batched: 4,096 texts, lengths log-uniform 1 KiB-16 MiB (7.27 GB), each with one of "
+                        "32 DFAs (states log-uniform 4-4096, alphabets 4/27/256, half keyword unions, half "
+                        "random); one persistent launch in a CUDA graph, autotuned segment size per DFA; "
+                        "counts and final states", n=0),
+    "d5": dict(workload="serving: 128 DFAs (states log-uniform 4-8192, alphabets 4/27/256, half keyword unions, "
+                        "half random), Poisson arrivals at 20,000 requests/s for 10 s, lengths log-uniform "
+                        "256 B-64 MiB, each request a slice of a 9 GiB device text arena; continuous batching "
+                        "server; counts and final states", n=0),
 }
 
 
@@ -62,9 +72,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(config):
-    """DRAM bytes per launch of the pass-1 kernel from a committed ncu summary, only when the
-    kernel sources are unchanged since the counters were taken."""
+def profiled_traffic(config, n, plan):
+    """DRAM bytes (read + write) per launch of the pass-1 kernel, from the committed ncu
+    summary of the same kernel sources and the same row plan (segment bytes, warps, blocks),
+    scaled from the captured text size to n bytes (a streaming kernel: traffic grows with the
+    text).  None when the sources or the plan differ."""
     p = os.path.join(ROOT, "profiles", f"traffic_{config}.json")
     if not os.path.exists(p):
         return None
@@ -72,7 +84,9 @@ def profiled_traffic(config):
         d = json.load(f)
     if d.get("kernel_hash") != kernel_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    if any(d.get(k) != plan.get(k) for k in ("segment_bytes", "warps_per_block", "blocks")):
+        return None
+    return int(round(d["dram_bytes_per_launch"] * n / d["text_bytes"]))
 
 
 # ---------------------------------------------------------------------------------------
@@ -224,6 +238,199 @@ def cpu_baseline(spec, text_dev, budget_s=12.0):
                       f"({r.match_count} matches, {dt:.1f} s)"}
 
 
+def run_batch(args, rank, world, local_rank):
+    """Batched configuration: one graph launch per step over all texts vs a loop of plain calls."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import paper_1412_1741_gb300 as pm
+    from paper_1412_1741_gb300 import workloads as wl
+
+    ge.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    n_texts = args.batch_texts
+    specs = wl.batch_dfas(32, seed=6)
+    lengths = wl.batch_lengths(n_texts, seed=6 + rank)
+    arena, offs = wl.batch_texts_device(specs, lengths, dev, seed=6 + rank)
+    dfas = [pm.parem_load_dfa(s.table, s.byte_to_symbol, s.start, s.accept) for s in specs]
+    ptr = arena.data_ptr()
+    items = [(dfas[i % len(dfas)], ptr + int(offs[i]), int(lengths[i]), None, 0) for i in range(n_texts)]
+    total = int(lengths.sum())
+    t0 = time.perf_counter()
+    batch = pm.parem_batch_create(items, pm.BatchOpts(autotune=1))
+    plan_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        batch.run()
+        b.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    step_ms = sorted(a.elapsed_time(b) for a, b in evs)
+    res = batch.results()
+    # plain: one parem_match per text on the same stream (same texts, same results)
+    for i in range(min(64, n_texts)):
+        pm.parem_match(items[i][0], items[i][1], length=items[i][2])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [pm.parem_match(it[0], it[1], length=it[2]) for it in items]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    agree = all((a.final_state, a.match_count) == (b.final_state, b.match_count) for a, b in zip(res, plain))
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    value = total * world * args.steps / (total_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = total / (step_ms[len(step_ms) // 2] / 1e3) / 1e9
+    segs = batch.segments()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": CONFIGS["d4"]["workload"], "texts": n_texts, "text_bytes": total, "dfas": len(dfas),
+                   "positions": "count only", "plan_seconds_with_autotune": round(plan_s, 3),
+                   "segment_bytes_median": int(np.median([s for s in segs if s] or [0])),
+                   "l2": "inputs larger than L2 (7.27 GB)", "parallelism": f"replicas x{world}"},
+        "p50_ms": round(step_ms[len(step_ms) // 2], 4),
+        "p99_ms": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
+        "batched_vs_plain": {"batched_gbs": round(value, 2), "plain_gbs": round(total / plain_s / 1e9, 2),
+                             "speedup": round(value / world / (total / plain_s / 1e9), 2),
+                             "plain_calls": n_texts, "results_agree": agree},
+        "roofline": {"bound": "hbm", "kernel": "whole batch graph (k_batch_scan + tiny kernel + copies)",
+                     "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None},
+        "gpu_launches": args.steps * 2,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.free()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving configuration: open-loop replay of a Poisson trace through the request server
+    (continuous batching), the same trace's head through the FIFO plain server, and a
+    saturation sweep over arrival rates."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import paper_1412_1741_gb300 as pm
+    from paper_1412_1741_gb300 import workloads as wl
+
+    ge.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    specs = wl.serve_dfas(128, seed=7)
+    dfas = [pm.parem_load_dfa(s.table, s.byte_to_symbol, s.start, s.accept) for s in specs]
+    pools = wl.serve_pools_device(dev, pool_bytes=1536 << 20, seed=7 + rank)
+    torch.cuda.synchronize()
+
+    def trace(rate, dur, seed):
+        arr, d, length = wl.serve_trace(len(specs), rate, dur, seed=seed)
+        return pm.make_requests(d, wl.serve_slices(specs, pools, d, length, seed=seed), length, arrival_ns=arr)
+
+    def summary(req, resp):
+        lat = (resp["done_ns"] - resp["arrival_ns"]) / 1e6
+        span = (resp["done_ns"].max() - resp["arrival_ns"].min()) / 1e9
+        return {"requests": int(len(req)), "bytes": int(req["len"].sum()),
+                "gbs": round(float(req["len"].sum()) / span / 1e9, 2), "span_s": round(span, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "errors": int((resp["status"] != 0).sum())}
+
+    srv = pm.parem_server_create(dfas)
+    for w in range(args.warmup):
+        srv.replay(trace(20000, 0.2, 100 + w))
+    k0 = srv.stats()["kernels"]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    duration = float(args.serve_seconds)
+    req = trace(20000, duration, 7 + rank)
+    resp = srv.replay(req)
+    clk = clocks.stop()
+    main = summary(req, resp)
+    kernels = srv.stats()["kernels"] - k0
+    st = srv.stats()
+    # saturation sweep: achieved throughput and p99 as the offered load grows
+    sweep = []
+    for rate in (20000, 40000, 80000, 160000):
+        r = trace(rate, 1.0, 500 + rate // 1000)
+        x = summary(r, srv.replay(r))
+        x["rate_per_s"] = rate
+        x["offered_gbs"] = round(float(r["len"].sum()) / 1.0 / 1e9, 2)
+        sweep.append(x)
+    srv.free()
+    # FIFO plain server on the head of the same trace (bounded: its backlog grows without limit
+    # once the offered load exceeds what one request at a time can serve)
+    head = req[req["arrival_ns"] < int(args.fifo_seconds * 1e9)]
+    fifo = pm.parem_server_create(dfas, pm.ServerOpts(mode=pm.PAREM_SERVE_FIFO))
+    fresp = fifo.replay(head)
+    fifo.free()
+    fsum = summary(head, fresp)
+    agree = bool(np.array_equal(fresp["final_state"], resp["final_state"][: len(head)]) and
+                 np.array_equal(fresp["match_count"], resp["match_count"][: len(head)]))
+    best = max(sweep, key=lambda x: x["gbs"])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": main["gbs"], "unit": "GB/s", "n_gpus": world, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": round(main["span_s"] * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": CONFIGS["d5"]["workload"], "dfas": len(dfas), "trace_seconds": duration,
+                       "requests": main["requests"], "text_bytes": main["bytes"], "positions": "count only",
+                       "l2": "inputs larger than L2 (9 GiB arena)", "parallelism": f"replicas x{world}",
+                       "step": "one replay of the whole trace"},
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "serving": {"batched": main, "batches": st["batches"], "max_batch": st["max_batch"],
+                        "fifo_plain": dict(fsum, trace_seconds=args.fifo_seconds), "fifo_results_agree": agree,
+                        "saturation_sweep": sweep, "max_sustained_gbs": best["gbs"]},
+            "e2e": {"value": main["gbs"], "unit": "GB/s", "h2d_bytes_per_step": int(len(req)) * 56,
+                    "d2h_bytes_per_step": int(len(req)) * 64,
+                    "note": "texts live in the device arena by design; each request's descriptor goes to the "
+                            "device and its result to the host; latency is arrival to result on the host"},
+            "roofline": {"bound": "hbm", "kernel": "k_batch_scan (continuous batches)", "achieved": main["gbs"],
+                         "peak": measured_peaks()[0], "unit": "GB/s",
+                         "frac": round(main["gbs"] / measured_peaks()[0], 4), "traffic": None},
+            "gpu_launches": int(kernels),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for d in dfas:
+        d.free()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -246,7 +453,7 @@ def run_ours(args, rank, world, local_rank):
     first = pm.parem_match(dfa, text)
     cap = max(1, first.match_count) if not args.count_only else 0
     pos = torch.empty(cap, dtype=torch.int64, device=dev) if cap else None
-    opts = pm.MatchOpts(record_kernel_times=1)
+    opts = pm.MatchOpts(record_kernel_times=1, segment_bytes=args.segment_bytes)
     for _ in range(args.warmup):
         pm.parem_match_ex(dfa, text, pos, opts)
     torch.cuda.synchronize()
@@ -306,7 +513,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / peak, 4), "frac_of_nominal_8000": round(achieved / 8000.0, 4),
                 "algorithmic_bytes_per_launch": n, "scan_ms_avg": round(scan_avg, 4),
                 "emit_ms_avg": round(sum(emit_ms) / len(emit_ms), 4),
-                "traffic": profiled_traffic(args.config),
+                "traffic": profiled_traffic(args.config, n, st),
             },
             "gpu_launches": kernels,
             "clocks": clk,
@@ -336,6 +543,100 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------------------
+# ncu summaries for profiles/ (read back from reports; no GPU needed)
+# ---------------------------------------------------------------------------------------
+NCU_METRICS = [
+    ("gpu__time_duration.sum", "duration"), ("dram__bytes_read.sum", "DRAM read"),
+    ("dram__bytes_write.sum", "DRAM write"), ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput %"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active %"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+    ("l1tex__throughput.avg.pct_of_peak_sustained_active", "L1/shared throughput %"),
+    ("l1tex__data_pipe_lsu_wavefronts_mem_shared_op_ld.sum", "shared-load wavefronts"),
+    ("l1tex__data_bank_conflicts_pipe_lsu_mem_shared_op_ld.sum", "shared-load bank conflicts"),
+    ("smsp__sass_inst_executed_op_shared_ld.sum", "shared-load instructions"),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active", "tensor pipe %"),
+    ("launch__registers_per_thread", "registers/thread"), ("launch__grid_size", "grid"),
+    ("launch__block_size", "block"), ("launch__shared_mem_per_block_dynamic", "dynamic smem/block"),
+]
+
+
+def _ncu_raw(rep):
+    import csv
+    import io
+    import subprocess
+
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True, check=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    return rows[0], rows[1], rows[2:]
+
+
+def summarize_ncu(args):
+    """Write profiles/<kernel>_<config>.md from a --set full report and, for the pass-1 kernel,
+    profiles/traffic_<config>.json (DRAM bytes of the captured launch, its text size and plan)."""
+    hdr, units, rows = _ncu_raw(args.ncu_report)
+    col = {h: i for i, h in enumerate(hdr)}
+    name = rows[0][col["Kernel Name"]]
+    base = name.split("<")[0].split("(")[0].split("::")[-1].split()[-1]
+    lines = [f"# {base} on {args.config} ({args.ncu_note})", "", "Command:", "", "```", args.ncu_command, "```", "",
+             f"Kernel: `{name[:160]}`", "", "| metric | value | unit |", "|---|---|---|"]
+    v = rows[0]
+    for m, label in NCU_METRICS:
+        if m in col:
+            lines.append(f"| {label} (`{m}`) | {v[col[m]]} | {units[col[m]]} |")
+    stalls = [(h[len("smsp__pcsamp_warps_issue_stalled_"):], float(v[i] or 0)) for h, i in col.items()
+              if h.startswith("smsp__pcsamp_warps_issue_stalled_") and not h.endswith("not_issued")]
+    tot = sum(x for _, x in stalls) or 1.0
+    top = sorted(stalls, key=lambda x: -x[1])[:6]
+    lines += ["", "Warp stall samples (top): " + ", ".join(f"{k} {100 * x / tot:.1f}%" for k, x in top)]
+    os.makedirs(os.path.join(ROOT, "profiles"), exist_ok=True)
+    path = os.path.join(ROOT, "profiles", f"{base}_{args.config}.md")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print("wrote", path)
+    if base == "k_spec_scan":
+        def num(m):
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(units[col[m]], 1)
+            return float(v[col[m]].replace(",", "")) * scale
+        d = {"kernel_hash": kernel_hash(), "config": args.config, "text_bytes": args.size_mb << 20,
+             "segment_bytes": args.segment_bytes, "warps_per_block": int(num("launch__block_size")) // 32,
+             "blocks": int(num("launch__grid_size")),
+             "dram_bytes_per_launch": int(num("dram__bytes_read.sum") + num("dram__bytes_write.sum")),
+             "source": os.path.basename(path)}
+        tp = os.path.join(ROOT, "profiles", f"traffic_{args.config}.json")
+        with open(tp, "w") as f:
+            json.dump(d, f, indent=1)
+        print("wrote", tp)
+
+
+def summarize_launches(args):
+    """Write profiles/launches_<config>.md from an ncu --csv launch list (gpu__time_duration.sum)."""
+    import csv
+
+    with open(args.ncu_launches) as f:
+        text = [ln for ln in f if not ln.startswith("==")]
+    rows = list(csv.DictReader(text))
+    per = {}
+    for r in rows:
+        if r.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        k = r["Kernel Name"].split("<")[0].split("(")[0].split("::")[-1].split()[-1]
+        scale = {"ns": 1e-6, "us": 1e-3, "usecond": 1e-3, "nsecond": 1e-6, "ms": 1.0, "msecond": 1.0}[r["Metric Unit"]]
+        t = float(r["Metric Value"].replace(",", "")) * scale
+        n, tot = per.get(k, (0, 0.0))
+        per[k] = (n + 1, tot + t)
+    total = sum(t for _, t in per.values()) or 1.0
+    lines = [f"# Launch list, {args.config} ({args.ncu_note})", "", "Command:", "", "```", args.ncu_command, "```", "",
+             "Per-launch times are cold-cache and serialised (ncu); the shares are what compare with the bench.", "",
+             "| kernel | launches | total ms | share |", "|---|---|---|---|"]
+    for k, (n, t) in sorted(per.items(), key=lambda x: -x[1][1]):
+        lines.append(f"| {k} | {n} | {t:.3f} | {100 * t / total:.1f}% |")
+    path = os.path.join(ROOT, "profiles", f"launches_{args.config}.md")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print("wrote", path)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,7 +649,22 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-sample-mb", type=int, default=256)
     ap.add_argument("--size-mb", type=int, default=0, help="override the text size (profiling captures)")
+    ap.add_argument("--segment-bytes", type=int, default=0,
+                    help="fix the row length (profiling captures of a smaller text with the full-size plan)")
+    ap.add_argument("--batch-texts", type=int, default=4096, help="texts of the batched configuration")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
+    ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
+    ap.add_argument("--ncu-report", default="", help="summarise this --set full report into profiles/")
+    ap.add_argument("--ncu-launches", default="", help="summarise this ncu --csv launch list into profiles/")
+    ap.add_argument("--ncu-command", default="", help="the command that made the report (recorded)")
+    ap.add_argument("--ncu-note", default="", help="what the capture covers (recorded)")
     args = ap.parse_args()
+    if args.ncu_report:
+        summarize_ncu(args)
+        return
+    if args.ncu_launches:
+        summarize_launches(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
@@ -359,6 +675,12 @@ def main():
         CONFIGS[args.config]["workload"] += f" (resized to {args.size_mb} MiB)"
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.config == "d4":
+        run_batch(args, rank, world, local_rank)
+        return
+    if args.config == "d5":
+        run_serve(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

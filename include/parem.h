@@ -84,7 +84,9 @@ typedef struct {
                                3 and 4: as 1 and 2 with 2-byte column offsets */
   uint32_t table_bytes;     /* bytes of the device transition table */
   uint32_t max_candidates;  /* largest candidate set |img(c) \ {dead}| over classes */
-  uint32_t reserved;
+  uint32_t sync_estimate;   /* symbols after which a candidate set has shrunk to one state on
+                               random input (median of seeded trials; 0 when no set has two
+                               states; 0xFFFFFFFF when a trial did not synchronise) */
   double mean_candidates;   /* mean candidate set size over the 256 byte values */
 } parem_dfa_info;
 
@@ -127,7 +129,10 @@ typedef struct {
   uint32_t kernels;         /* kernels launched by the call */
   uint32_t emit_replays;    /* rows whose positions the emit pass replayed (not recorded in pass 1) */
   uint32_t emit_max_window; /* longest window (bytes) the emit pass replayed */
-  uint32_t reserved;
+  uint32_t nonconv_rows;    /* rows whose candidates did not merge within the speculation cap
+                               (they fall back to per-candidate slot maps) */
+  uint32_t conv_max;        /* longest speculative prefix a row needed before its candidates
+                               merged (bytes); later plans for the DFA use longer rows */
 } parem_stats;
 
 /*
@@ -211,9 +216,10 @@ int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, ui
  * no cudaMalloc, cudaFree or other allocating routine.
  *   Arguments, results and errors are those of parem_match, plus PAREM_ERR_TOO_LARGE when
  *   the scan of this text would need more scratch than the fixed area holds: 8 bytes per
- *   32-row chunk, 112 bytes per row when positions are requested, and 8 bytes per candidate
- *   per row for the slot maps (with the default plan: about 400 MiB of text for an
- *   Aho-Corasick DFA with 47 candidates per class, far more for small candidate sets).
+ *   32-row chunk, 112 bytes per row when positions are requested, and, for DFAs whose
+ *   unmerged rows go through slot maps (at most 32 candidates, or no synchronisation), 8
+ *   bytes per candidate per row.  With the default plan a 16 MiB area holds hundreds of MiB
+ *   of text for the count, and about 100-150 MiB when positions are requested.
  *   Nothing is written to the outputs in that case.
  *   Every GPU that loads the library holds the array until the process exits.  The first
  *   call on a device looks up the array's device address (cudaGetSymbolAddress, with that
@@ -224,6 +230,152 @@ int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, ui
  */
 int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                         uint64_t capacity, void* stream, parem_result* out);
+
+/*
+ * Batched matching: many (text, DFA) pairs in one persistent launch.
+ *
+ * The batch is planned once (parem_batch_create) and run any number of times
+ * (parem_batch_run), e.g. after the caller refills the same text buffers.  Planning assigns
+ * each item its rows of S bytes, lays out every item's scratch in one allocation, writes the
+ * per-item descriptors (scan parameters and TMA tensor maps) to device memory, and captures
+ * the work (clearing the scratch, the persistent scan kernel, the emit kernel, the copy of
+ * the results to pinned host memory) into one CUDA graph.  In the persistent kernel each
+ * thread block serves one DFA at a time, with that DFA's table staged in shared memory (or
+ * read from L2 when it is too large), and moves to another DFA when the first runs out of
+ * chunks.  Every item's result is exactly that of parem_match on it (Algorithm 1 per item).
+ */
+typedef struct parem_batch parem_batch;
+
+typedef struct {
+  const parem_dfa* dfa;   /* loaded on the current device */
+  const uint8_t* text;    /* device pointer, any alignment (NULL when len == 0) */
+  uint64_t len;
+  uint64_t* positions;    /* device pointer or NULL (count only) */
+  uint64_t capacity;      /* slots in positions */
+} parem_batch_item;
+
+typedef struct {
+  uint32_t autotune;        /* 1: choose each DFA's segment size by timing candidates on its own
+                               items (several trial runs during parem_batch_create) */
+  uint32_t warps_per_block; /* 0 = 24 */
+  uint64_t segment_bytes;   /* 0 = planner/autotuner; else the same S for every item */
+  uint32_t use_graph;       /* 0: launch the kernels directly in parem_batch_run; else (default
+                               when the struct is NULL) replay the captured CUDA graph */
+  uint32_t reserved;
+} parem_batch_opts;
+
+/* Plan a batch of n_items items (host array, copied) on the current device.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+int parem_batch_create(const parem_batch_item* items, uint32_t n_items, const parem_batch_opts* opts,
+                       parem_batch** out);
+
+/* Run the batch on `stream` and wait for it.  Errors: CUDA, TIMEOUT, INTERNAL; CAPACITY when some
+ * item had more matches than its capacity (its result is still exact). */
+int parem_batch_run(parem_batch* batch, void* stream);
+
+/* Results of the last run, in the order of the items given to parem_batch_create. */
+int parem_batch_results(const parem_batch* batch, parem_result* out);
+
+/* Segment size chosen for item i (planner or autotuner).  Errors: INVALID_ARG. */
+int parem_batch_item_segment(const parem_batch* batch, uint32_t i, uint64_t* segment_bytes);
+
+/* Free a batch (NULL is ignored). */
+void parem_batch_free(parem_batch* batch);
+
+/*
+ * Request server: continuous batching of independent match requests.
+ *
+ * Algorithm 1 applies to each request on its own (every response equals parem_match on that
+ * request); the server only decides which requests share a launch.  A dispatcher thread
+ * takes the waiting requests in arrival order, as many as fit one batch (a request-count and
+ * a text-byte limit, and the scratch and descriptor space of a pre-allocated arena: memory
+ * admission), plans them into the arena and launches the batch kernels on that arena's
+ * stream.  With two or more arenas the next batch is launched while the previous one runs,
+ * so requests that arrive meanwhile start as soon as thread blocks of the running batch
+ * retire.  A completion thread waits for the batches in launch order and queues their
+ * responses.  Nothing is allocated per request or per batch.  Mode PAREM_SERVE_FIFO instead
+ * runs the requests one at a time through parem_match, in arrival order (the plain
+ * comparison).
+ *
+ * Texts and position buffers are device memory owned by the caller; they must stay valid
+ * until the request's response has been polled.  Timestamps are nanoseconds of the steady
+ * clock that parem_clock_ns reads.
+ */
+typedef struct parem_server parem_server;
+
+#define PAREM_SERVE_BATCH 0u
+#define PAREM_SERVE_FIFO 1u
+
+typedef struct {
+  uint32_t mode;                 /* PAREM_SERVE_BATCH (default) or PAREM_SERVE_FIFO */
+  uint32_t arenas;               /* batches in flight (0 = 2) */
+  uint32_t max_items;            /* requests per batch (0 = 4096) */
+  uint32_t reserved0;
+  uint64_t max_batch_bytes;      /* text bytes per batch (0 = 1 GiB) */
+  uint64_t arena_scratch_bytes;  /* device scratch per arena (0 = 256 MiB) */
+  uint64_t reserved[4];
+} parem_server_opts;
+
+typedef struct {
+  uint32_t dfa_index;        /* index into the DFAs given to parem_server_create */
+  uint32_t reserved0;
+  const uint8_t* text;       /* device */
+  uint64_t len;
+  uint64_t* positions;       /* device, or NULL for the count only */
+  uint64_t capacity;
+  uint64_t tag;              /* returned in the response */
+  int64_t arrival_ns;        /* arrival time (steady clock); 0 = the time of submission */
+} parem_request;
+
+typedef struct {
+  uint64_t tag;
+  int32_t status;            /* as parem_match: OK, CAPACITY, TIMEOUT, INTERNAL, TOO_LARGE (the
+                                request alone exceeds an arena), INVALID_ARG */
+  uint32_t batch_size;       /* requests in the launch that served this one */
+  parem_result result;
+  int64_t arrival_ns;
+  int64_t launch_ns;         /* when its batch was launched */
+  int64_t done_ns;           /* when its result was on the host */
+} parem_response;
+
+typedef struct {
+  uint64_t submitted, answered, batches, bytes;
+  uint64_t max_batch;        /* largest batch launched */
+  uint64_t kernels;          /* kernel launches so far */
+  uint64_t reserved[2];
+} parem_server_stats;
+
+/* Create a server for n_dfas loaded DFAs (all on the current device; the array is copied, the
+ * DFAs stay owned by the caller and must outlive the server).  Allocates the arenas, streams
+ * and threads.  Errors: INVALID_ARG, OOM, CUDA. */
+int parem_server_create(parem_dfa* const* dfas, uint32_t n_dfas, const parem_server_opts* opts,
+                        parem_server** out);
+
+/* Queue n requests (host array, copied).  Errors: INVALID_ARG (a bad DFA index or null text;
+ * nothing is queued). */
+int parem_server_submit(parem_server* srv, const parem_request* reqs, uint32_t n);
+
+/* Move up to max finished responses into out (in completion order); *n_out is their number.
+ * Waits up to wait_ns for the first one (0 = do not wait).  Errors: INVALID_ARG. */
+int parem_server_poll(parem_server* srv, parem_response* out, uint32_t max, uint32_t* n_out, int64_t wait_ns);
+
+/* Wait until every submitted request has a response waiting to be polled. */
+int parem_server_drain(parem_server* srv);
+
+/* Open-loop trace replay: submit reqs[i] at (start + reqs[i].arrival_ns) from a library thread,
+ * where start is the time of the call, and wait for all of them; out[i] is reqs[i]'s response
+ * (the tags are replaced by i).  Responses queued before the call are kept for
+ * parem_server_poll.  Errors: INVALID_ARG, and the first failing request's status is not an
+ * error of the call (read out[i].status). */
+int parem_server_replay(parem_server* srv, const parem_request* reqs, uint32_t n, parem_response* out);
+
+int parem_server_get_stats(const parem_server* srv, parem_server_stats* out);
+
+/* Stop the threads after the submitted requests have been served, and free the server. */
+void parem_server_free(parem_server* srv);
+
+/* The steady clock the server stamps responses with (nanoseconds). */
+int64_t parem_clock_ns(void);
 
 /* Plan and kernel times of the last scan issued on (current device, stream); waits for the
  * recorded events.  Errors: INVALID_ARG (no scan yet), CUDA. */

@@ -26,7 +26,9 @@ __all__ = [
     "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa",
     "parem_match", "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror",
     "parem_version", "parem_last_stats", "parem_match_noalloc", "Stats", "EXPORTED_SYMBOLS",
-    "PAREM_ERR_TOO_LARGE", "PAREM_NOALLOC_SCRATCH_BYTES",
+    "PAREM_ERR_TOO_LARGE", "PAREM_NOALLOC_SCRATCH_BYTES", "parem_batch_create", "Batch", "BatchOpts",
+    "parem_server_create", "Server", "ServerOpts", "make_requests", "parem_clock_ns", "REQUEST_DTYPE",
+    "RESPONSE_DTYPE", "PAREM_SERVE_BATCH", "PAREM_SERVE_FIFO",
 ]
 
 PAREM_NONE = 0xFFFFFFFF
@@ -43,7 +45,10 @@ _LIB = None
 EXPORTED_SYMBOLS = [
     "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
-    "parem_last_stats", "parem_match_noalloc",
+    "parem_last_stats", "parem_match_noalloc", "parem_batch_create", "parem_batch_run", "parem_batch_results",
+    "parem_batch_item_segment", "parem_batch_free", "parem_server_create", "parem_server_submit",
+    "parem_server_poll", "parem_server_drain", "parem_server_replay", "parem_server_get_stats",
+    "parem_server_free", "parem_clock_ns",
 ]
 
 
@@ -64,7 +69,7 @@ class _Info(ctypes.Structure):
                 ("compact_states", ctypes.c_uint32), ("n_classes", ctypes.c_uint32),
                 ("has_dead", ctypes.c_uint32), ("entry_bytes", ctypes.c_uint32),
                 ("layout", ctypes.c_uint32), ("table_bytes", ctypes.c_uint32),
-                ("max_candidates", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("max_candidates", ctypes.c_uint32), ("sync_estimate", ctypes.c_uint32),
                 ("mean_candidates", ctypes.c_double)]
 
 
@@ -86,7 +91,8 @@ class Stats(ctypes.Structure):
                 ("rows", ctypes.c_uint64), ("chunks", ctypes.c_uint64), ("blocks", ctypes.c_uint32),
                 ("warps_per_block", ctypes.c_uint32), ("candidate_regs", ctypes.c_uint32),
                 ("spec_cap_bytes", ctypes.c_uint32), ("kernels", ctypes.c_uint32),
-                ("emit_replays", ctypes.c_uint32), ("emit_max_window", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("emit_replays", ctypes.c_uint32), ("emit_max_window", ctypes.c_uint32),
+                ("nonconv_rows", ctypes.c_uint32), ("conv_max", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -113,6 +119,7 @@ class DfaInfo:
     table_bytes: int
     max_candidates: int
     mean_candidates: float
+    sync_estimate: int = 0
 
 
 def library_path() -> str:
@@ -198,7 +205,7 @@ class Dfa:
 
 def _info(i: _Info) -> DfaInfo:
     return DfaInfo(i.n_states, i.n_symbols, i.compact_states, i.n_classes, bool(i.has_dead), i.entry_bytes,
-                   i.layout, i.table_bytes, i.max_candidates, i.mean_candidates)
+                   i.layout, i.table_bytes, i.max_candidates, i.mean_candidates, i.sync_estimate)
 
 
 def parem_prepare_info(table, byte_to_symbol, start, accept) -> DfaInfo:
@@ -327,3 +334,241 @@ def parem_match_noalloc(dfa: Dfa, text, positions=None, stream=None, length=None
     res = _Result()
     rc = lib.parem_match_noalloc(dfa.handle, tp, n, pp, cap, _stream(stream), ctypes.byref(res))
     return _finish(rc, res, "parem_match_noalloc")
+
+
+# ---------------------------------------------------------------------------------------
+# batched matching
+# ---------------------------------------------------------------------------------------
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("dfa", ctypes.c_void_p), ("text", ctypes.c_void_p), ("len", ctypes.c_uint64),
+                ("positions", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("segment_bytes", ctypes.c_uint64), ("use_graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def __init__(self, autotune=0, warps_per_block=0, segment_bytes=0, use_graph=1):
+        super().__init__(autotune, warps_per_block, segment_bytes, use_graph, 0)
+
+
+def _bind_batch(lib):
+    if getattr(lib, "_batch_bound", False):
+        return
+    vp = ctypes.c_void_p
+    lib.parem_batch_create.argtypes = [ctypes.POINTER(_BatchItem), ctypes.c_uint32, ctypes.POINTER(BatchOpts),
+                                       ctypes.POINTER(vp)]
+    lib.parem_batch_create.restype = ctypes.c_int
+    lib.parem_batch_run.argtypes = [vp, vp]
+    lib.parem_batch_run.restype = ctypes.c_int
+    lib.parem_batch_results.argtypes = [vp, ctypes.POINTER(_Result)]
+    lib.parem_batch_results.restype = ctypes.c_int
+    lib.parem_batch_item_segment.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.parem_batch_item_segment.restype = ctypes.c_int
+    lib.parem_batch_free.argtypes = [vp]
+    lib.parem_batch_free.restype = None
+    lib._batch_bound = True
+
+
+class Batch:
+    """A planned batch (parem_batch*): run() replays it; results() in the order given."""
+
+    def __init__(self, handle, n, keep):
+        self._h = handle
+        self.n = n
+        self._keep = keep  # the tensors whose memory the batch refers to
+
+    def run(self, stream=None) -> int:
+        lib = load_library()
+        rc = lib.parem_batch_run(self._h, _stream(stream))
+        if rc not in (PAREM_OK, PAREM_ERR_CAPACITY):
+            raise ParemError(rc, "parem_batch_run")
+        return rc
+
+    def results(self):
+        lib = load_library()
+        arr = (_Result * self.n)()
+        rc = lib.parem_batch_results(self._h, arr)
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_batch_results")
+        return [MatchResult(r.final_state, bool(r.accepted), r.match_count, r.n_written) for r in arr]
+
+    def segments(self):
+        lib = load_library()
+        out = []
+        v = ctypes.c_uint64()
+        for i in range(self.n):
+            lib.parem_batch_item_segment(self._h, i, ctypes.byref(v))
+            out.append(v.value)
+        return out
+
+    def free(self):
+        if self._h is not None:
+            load_library().parem_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def parem_batch_create(items, opts: BatchOpts | None = None) -> Batch:
+    """items: sequence of (dfa, text, positions_or_None) with CUDA tensors (or
+    (dfa, text_ptr, length, positions_ptr, capacity) tuples of raw device pointers)."""
+    lib = load_library()
+    _bind_batch(lib)
+    arr = (_BatchItem * len(items))()
+    keep = []
+    for i, it in enumerate(items):
+        if len(it) == 5:
+            dfa, tp, n, pp, cap = it
+        else:
+            dfa, text, pos = it
+            tp, n = _ptr_len(text)
+            pp, pb = _ptr_len(pos)
+            cap = pb // 8 if pp else 0
+            keep.append((text, pos))
+        arr[i] = _BatchItem(dfa.handle, tp, n, pp, cap)
+    h = ctypes.c_void_p()
+    rc = lib.parem_batch_create(arr, len(items), None if opts is None else ctypes.byref(opts), ctypes.byref(h))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_batch_create")
+    return Batch(h, len(items), keep)
+
+
+# ---------------------------------------------------------------------------------------
+# request server (continuous batching)
+# ---------------------------------------------------------------------------------------
+PAREM_SERVE_BATCH = 0
+PAREM_SERVE_FIFO = 1
+
+# parem_request and parem_response as numpy records (the C layouts, 56 and 64 bytes)
+REQUEST_DTYPE = np.dtype({
+    "names": ["dfa_index", "text", "len", "positions", "capacity", "tag", "arrival_ns"],
+    "formats": [np.uint32, np.uint64, np.uint64, np.uint64, np.uint64, np.uint64, np.int64],
+    "offsets": [0, 8, 16, 24, 32, 40, 48], "itemsize": 56})
+RESPONSE_DTYPE = np.dtype({
+    "names": ["tag", "status", "batch_size", "final_state", "accepted", "match_count", "n_written",
+              "arrival_ns", "launch_ns", "done_ns"],
+    "formats": [np.uint64, np.int32, np.uint32, np.uint32, np.uint8, np.uint64, np.uint64,
+                np.int64, np.int64, np.int64],
+    "offsets": [0, 8, 12, 16, 20, 24, 32, 40, 48, 56], "itemsize": 64})
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("arenas", ctypes.c_uint32), ("max_items", ctypes.c_uint32),
+                ("reserved0", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
+                ("arena_scratch_bytes", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
+
+    def __init__(self, mode=PAREM_SERVE_BATCH, arenas=0, max_items=0, max_batch_bytes=0, arena_scratch_bytes=0):
+        super().__init__(mode, arenas, max_items, 0, max_batch_bytes, arena_scratch_bytes)
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("answered", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint64), ("kernels", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64 * 2)]
+
+
+def _bind_server(lib):
+    if getattr(lib, "_server_bound", False):
+        return
+    vp, u32 = ctypes.c_void_p, ctypes.c_uint32
+    lib.parem_server_create.argtypes = [ctypes.POINTER(vp), u32, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    lib.parem_server_submit.argtypes = [vp, vp, u32]
+    lib.parem_server_poll.argtypes = [vp, vp, u32, ctypes.POINTER(u32), ctypes.c_int64]
+    lib.parem_server_drain.argtypes = [vp]
+    lib.parem_server_replay.argtypes = [vp, vp, u32, vp]
+    lib.parem_server_get_stats.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+    for f in ("parem_server_create", "parem_server_submit", "parem_server_poll", "parem_server_drain",
+              "parem_server_replay", "parem_server_get_stats"):
+        getattr(lib, f).restype = ctypes.c_int
+    lib.parem_server_free.argtypes = [vp]
+    lib.parem_server_free.restype = None
+    lib.parem_clock_ns.argtypes = []
+    lib.parem_clock_ns.restype = ctypes.c_int64
+    lib._server_bound = True
+
+
+def make_requests(dfa_index, text_ptr, length, positions_ptr=0, capacity=0, tag=None, arrival_ns=0):
+    """Vectorised construction of a parem_request array (device addresses as integers)."""
+    n = len(np.atleast_1d(length))
+    r = np.zeros(n, dtype=REQUEST_DTYPE)
+    r["dfa_index"] = dfa_index
+    r["text"] = text_ptr
+    r["len"] = length
+    r["positions"] = positions_ptr
+    r["capacity"] = capacity
+    r["tag"] = np.arange(n, dtype=np.uint64) if tag is None else tag
+    r["arrival_ns"] = arrival_ns
+    return r
+
+
+class Server:
+    """A request server (parem_server*): submit()/poll() or an open-loop replay() of a trace."""
+
+    def __init__(self, handle, dfas):
+        self._h = handle
+        self._dfas = list(dfas)  # the DFAs must outlive the server
+
+    def submit(self, requests) -> None:
+        req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+        rc = load_library().parem_server_submit(self._h, req.ctypes.data, len(req))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_server_submit")
+
+    def poll(self, max_n=4096, wait_s=0.0):
+        out = np.zeros(max_n, dtype=RESPONSE_DTYPE)
+        got = ctypes.c_uint32()
+        rc = load_library().parem_server_poll(self._h, out.ctypes.data, max_n, ctypes.byref(got), int(wait_s * 1e9))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_server_poll")
+        return out[: got.value]
+
+    def drain(self) -> None:
+        load_library().parem_server_drain(self._h)
+
+    def replay(self, requests):
+        """Submit requests[i] at (call time + requests[i]['arrival_ns']); returns the responses in
+        request order."""
+        req = np.ascontiguousarray(requests, dtype=REQUEST_DTYPE)
+        out = np.zeros(len(req), dtype=RESPONSE_DTYPE)
+        rc = load_library().parem_server_replay(self._h, req.ctypes.data, len(req), out.ctypes.data)
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_server_replay")
+        return out
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        load_library().parem_server_get_stats(self._h, ctypes.byref(st))
+        return {k: getattr(st, k) for k in ("submitted", "answered", "batches", "bytes", "max_batch", "kernels")}
+
+    def free(self):
+        if self._h is not None:
+            load_library().parem_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def parem_server_create(dfas, opts: ServerOpts | None = None) -> Server:
+    lib = load_library()
+    _bind_server(lib)
+    arr = (ctypes.c_void_p * len(dfas))(*[d.handle for d in dfas])
+    h = ctypes.c_void_p()
+    rc = lib.parem_server_create(arr, len(dfas), None if opts is None else ctypes.byref(opts), ctypes.byref(h))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_server_create")
+    return Server(h, dfas)
+
+
+def parem_clock_ns() -> int:
+    lib = load_library()
+    _bind_server(lib)
+    return lib.parem_clock_ns()

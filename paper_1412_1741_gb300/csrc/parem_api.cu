@@ -21,7 +21,7 @@ using namespace parem;
 
 namespace {
 
-constexpr uint32_t kSmemTableBudget = 96 * 1024;
+constexpr uint32_t kSmemTableBudget = 160 * 1024;
 
 #define PAREM_CUDA_TRY(expr)                              \
   do {                                                    \
@@ -135,6 +135,7 @@ void fill_info(const Prepared& P, parem_dfa_info* info) {
   info->table_bytes = P.table_bytes;
   info->max_candidates = P.max_cand;
   info->mean_candidates = P.mean_cand;
+  info->sync_estimate = P.sync_len;
 }
 
 }  // namespace
@@ -258,6 +259,7 @@ extern "C" void parem_free_dfa(parem_dfa* dfa) {
   if (!dfa) return;
   cudaDeviceSynchronize();
   if (dfa->dmem) cudaFree(dfa->dmem);
+  if (dfa->batch_mem) cudaFree(dfa->batch_mem);
   delete dfa;
 }
 
@@ -315,6 +317,44 @@ extern "C" int parem_release_scratch(void* stream) {
 // ---------------------------------------------------------------------------------------
 namespace parem {
 
+// Row length in units of the synchronisation length (measured: see the planner notes).
+constexpr uint64_t kRowsPerSync = 8;
+
+bool serial_rows(const parem_dfa* dfa, uint32_t m) { return m > kLanes && dfa->host.sync_len != kNoSync; }
+
+uint64_t max_row_bytes(const parem_dfa* dfa, uint32_t m) {
+  // An unmerged row run from its resolved start costs S lookups on the chunk's warp.
+  if (serial_rows(dfa, m)) return 16u << 20;
+  // Through slot maps it costs m * S lookups; bound that to 2^27 lookups so that even a text
+  // that never synchronises the automaton keeps every chunk well inside the device wait limit.
+  return std::max<uint64_t>(4096, ((1ull << 27) / std::max<uint32_t>(m, 1)) / kBox * kBox);
+}
+
+uint64_t min_row_bytes(const parem_dfa* dfa, uint32_t P) {
+  const Prepared& H = dfa->host;
+  uint64_t smin = P == 1 ? 512 : 4096;
+  // rows several times longer than the candidates need to merge: the estimate from random
+  // input (prepare time) or the longest merge seen on real input, whichever is larger
+  const uint64_t est = H.sync_len == kNoSync ? 0 : H.sync_len;
+  smin = std::max<uint64_t>(smin, kRowsPerSync * std::max<uint64_t>(est, dfa->conv_hint.load()));
+  smin = std::min<uint64_t>(round_up(smin, kBox), 64u << 20);
+  return std::min(smin, max_row_bytes(dfa, H.max_cand));
+}
+
+void learn_convergence(const parem_dfa* dfa, uint32_t spec_cap, uint32_t nonconv_rows, uint32_t conv_max) {
+  // Only DFAs whose candidates do merge teach anything: when some rows merged and others ran
+  // out of the speculation cap, the next plans get a larger cap (4x) and longer rows (8x). A
+  // DFA whose rows never merge (a permutation automaton) keeps its plan: longer rows would
+  // not make its slot maps cheaper.
+  if (conv_max == 0) return;
+  uint32_t want = nonconv_rows ? std::max(conv_max, spec_cap) : conv_max;
+  want = std::min<uint32_t>(want, 1u << 24);
+  auto& h = const_cast<parem_dfa*>(dfa)->conv_hint;
+  uint32_t cur = h.load();
+  while (want > cur && !h.compare_exchange_weak(cur, want)) {
+  }
+}
+
 int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const parem_match_opts* o,
               Plan* pl) {
   const Prepared& P = dfa->host;
@@ -324,6 +364,7 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   const uint32_t m_need = pl->enum_all ? (P.n - P.has_dead) : P.max_cand;
   pl->P = m_need <= 32 ? 1 : m_need <= 64 ? 2 : m_need <= 128 ? 4 : 8;
   pl->cand_stride = std::max<uint32_t>(1, std::max(P.max_cand, pl->enum_all ? P.n : 0u));
+  pl->serial = serial_rows(dfa, m_need) ? 1u : 0u;
   // lanes per row in the grouped speculation (P == 1): the smallest power of two that holds
   // the largest candidate set
   pl->group = 1;
@@ -353,10 +394,11 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   if (o && o->segment_bytes) {
     S = round_up(o->segment_bytes, kBox);
   } else {
-    const uint64_t smin = pl->P == 1 ? 512 : 4096;
+    const uint64_t smax = max_row_bytes(dfa, m_need);
+    const uint64_t smin = std::min(min_row_bytes(dfa, pl->P), smax);
     S = round_up(std::max<uint64_t>(body / (lanes_total * 2 + 1), 1), kBox);
     S = std::max(S, smin);
-    S = std::min<uint64_t>(S, 1u << 20);
+    S = std::min<uint64_t>(S, std::max<uint64_t>(smin, std::min<uint64_t>(smax, 1u << 20)));
   }
   // keep the row index inside the TMA coordinate range
   while (body / S >= (1ull << 31)) S *= 2;
@@ -365,7 +407,21 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   pl->R = S ? body / S : 0;
   pl->tail = S ? body - pl->R * S : body;
   pl->n_chunks = (pl->R + kLanes - 1) / kLanes;
-  uint64_t cap = o && o->spec_cap_bytes ? o->spec_cap_bytes : std::max<uint64_t>(2048, 16ull * P.n);
+  // Fewer chunks than warps: warps take chunks in ticket order, and the warps of the first
+  // blocks would take them all, crowding a few SMs.  Spread them: one block per chunk up to
+  // the SM count, then as many warps per block as the chunks need.
+  if (!(o && o->warps_per_block) && pl->n_chunks < (uint64_t)pl->grid * pl->warps) {
+    if (pl->n_chunks <= (uint64_t)pl->grid) {
+      pl->grid = (int)std::max<uint64_t>(1, pl->n_chunks);
+      pl->warps = 1;
+    } else {
+      pl->warps = (int)((pl->n_chunks + pl->grid - 1) / pl->grid);
+    }
+    pl->smem = fixed + (size_t)pl->warps * per_warp;
+  }
+  uint64_t cap = o && o->spec_cap_bytes ? o->spec_cap_bytes
+                                        : std::max<uint64_t>(std::max<uint64_t>(2048, 16ull * P.n),
+                                                             4ull * dfa->conv_hint.load());
   cap = std::min<uint64_t>(cap, S);
   pl->spec_cap = (uint32_t)(cap / 16 * 16);
   if (pl->spec_cap == 0) pl->spec_cap = 16;
@@ -402,7 +458,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const uint64_t o_segrec = round_up(o_status + pl.n_chunks * 8, 256);
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
-  const uint64_t slot_bytes = pl.R * (uint64_t)pl.cand_stride * 4;
+  const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
   const uint64_t total = round_up(o_slot + 2 * slot_bytes, 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
@@ -427,6 +483,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.enum_all = pl.enum_all;
   p.spec_cap = pl.spec_cap;
   p.cand_stride = pl.cand_stride;
+  p.serial_fallback = pl.serial;
   p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
   p.skip_publish = o ? o->debug_skip_publish_chunk : -1;
   if (!o) p.skip_publish = -1;
@@ -482,6 +539,9 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const DevResult r = *sc->host_res;
   sc->stats.emit_replays = r.emit_replays;
   sc->stats.emit_max_window = r.emit_max_window;
+  sc->stats.nonconv_rows = r.nonconv_rows;
+  sc->stats.conv_max = r.conv_max;
+  if (pl.R) learn_convergence(dfa, pl.spec_cap, r.nonconv_rows, r.conv_max);
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
   const uint32_t fs = r.final_state;

@@ -27,7 +27,11 @@ constexpr uint64_t kMaxText = 1ull << 45;
 
 // Table layouts (parem_dfa_info.layout).  The class layouts read a 256-entry byte -> column
 // map; its entries are u8 when every column offset fits a byte, else u16 (the *W layouts).
-enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClassSmemW = 3, kClassGlobalW = 4 };
+enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClassSmemW = 3, kClassGlobalW = 4,
+                         // batch kernels: class-indexed u16 table with a u16 column map, staged in
+                         // shared memory or read from global memory as each DFA requires
+                         kBatchDyn = 5 };
+constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
 // Shared memory of every kernel starts with the column map (512 B reserved) followed by the
 // table at this fixed offset, so table reads use an immediate offset.
 constexpr uint32_t kTableOff = 512;
@@ -56,6 +60,7 @@ struct Prepared {
   uint32_t layout = 0, esize = 1, rowbytes = 0, table_bytes = 0;
   uint32_t max_cand = 0;            // over byte classes
   double mean_cand = 0;
+  uint32_t sync_len = 0;            // estimated synchronisation length (symbols), or kNoSync
   std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
   std::vector<uint32_t> compact_of; // original -> compact
   std::vector<uint16_t> byte_class; // 256
@@ -107,6 +112,11 @@ struct DevResult {
   uint64_t count;
   uint32_t emit_replays;     // rows whose positions the emit pass had to replay
   uint32_t emit_max_window;  // longest replayed window (bytes)
+  uint32_t nonconv_rows;     // rows whose candidates did not merge within the speculation cap
+  uint32_t conv_max;         // longest merged prefix t over the rows (bytes)
+  uint32_t progress;         // bumped by long serial steps; device waits time out only
+                             // when it has not moved for their whole budget
+  uint32_t pad;
 };
 
 // Parameters of one plain scan (one text).
@@ -126,6 +136,8 @@ struct ScanParams {
   uint32_t enum_all;       // candidates = all live states
   uint32_t spec_cap;       // bytes of speculation before a segment counts as non-converged
   uint32_t cand_stride;    // slots per segment in the slot map
+  uint32_t serial_fallback;  // rows that did not merge are run from their resolved start
+                             // (no slot maps); else every candidate gets a slot-map entry
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch
@@ -142,6 +154,42 @@ struct ScanParams {
   // shared memory: [colmap | table at kTableOff] then, from the first 1024-aligned address
   // at or after kTableOff + smem_table_bytes: per-warp stages, barriers and speculation scratch
   uint32_t smem_table_bytes;
+};
+
+// ---------------------------------------------------------------------------------------
+// Batch: many (text, DFA) items in one persistent launch.
+// ---------------------------------------------------------------------------------------
+// One DFA of a batch ("slot"): its items are contiguous in the item array.
+struct BatchSlot {
+  DeviceDfa dfa;           // kBatchDyn copy: u16 class table, u16 column map
+  uint32_t smem_tier;      // 1: the table is staged in shared memory
+  uint32_t item_begin, item_end;
+  uint32_t pad;
+  uint64_t n_chunks;       // chunks of all its items
+  uint64_t n_rows;         // rows of all its items
+  uint32_t* ticket;        // chunk ticket counter of the slot
+};
+
+// One (text, DFA) item: its scan parameters (scratch pointers inside the batch scratch) and
+// the tensor map of its rows.  64-byte aligned for the tensor map.
+struct alignas(64) BatchItem {
+  CUtensorMap tmap;
+  ScanParams p;
+  uint64_t chunk_base;     // first chunk ticket of the item within its slot
+  uint64_t row_base;       // first row of the item within its slot
+};
+
+struct BatchParams {
+  const BatchItem* items;
+  const BatchSlot* slots;
+  const uint32_t* cta_slot;     // first slot of each persistent CTA of the scan kernel
+  const uint32_t* emit_slot;    // slot of each CTA of the emit kernel
+  const uint64_t* emit_row0;    // first row (within the slot) of each CTA of the emit kernel
+  uint32_t n_slots;
+  uint32_t max_table_smem;      // largest table staged in shared memory (carve-up)
+  uint32_t spec_bytes;          // per-warp speculation scratch (largest over the slots)
+  uint32_t pad;
+  uint64_t wait_budget;
 };
 
 }  // namespace parem

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "parem_internal.h"
 
 #include "../../include/parem.h"
@@ -15,7 +17,28 @@ struct parem_dfa {
   parem::DeviceDfa dev{};
   void* dmem = nullptr;
   parem_dfa_info info{};
+  // the batch kernels' copy (u16 class table, u16 column map), built on first batch use
+  parem::DeviceDfa batch{};
+  void* batch_mem = nullptr;
+  // longest speculative prefix (bytes) the candidates of this DFA needed so far, learned from
+  // earlier scans; plans make rows several times longer than this
+  std::atomic<uint32_t> conv_hint{0};
 };
+
+namespace parem {
+// Shortest row length worth speculating for this DFA: a multiple of its learned convergence
+// length, or for DFAs whose candidate sets are large relative to their states (random-like
+// automata, which need about twice their state count to synchronise) a multiple of n.
+uint64_t min_row_bytes(const parem_dfa* dfa, uint32_t P);
+// Longest row worth planning for m candidates: bounds the slot-map cost of a row whose
+// candidates never merge.
+uint64_t max_row_bytes(const parem_dfa* dfa, uint32_t m);
+// Rows whose candidates have not merged are run from their resolved start instead of through
+// slot maps: for more candidates than one pass of the lanes, when the DFA synchronises.
+bool serial_rows(const parem_dfa* dfa, uint32_t m);
+// Record what a scan with the given speculation cap observed about convergence.
+void learn_convergence(const parem_dfa* dfa, uint32_t spec_cap, uint32_t nonconv_rows, uint32_t conv_max);
+}  // namespace parem
 
 namespace parem {
 
@@ -31,6 +54,7 @@ struct Plan {
   size_t smem;
   uint64_t h, S, R, tail, n_chunks;
   uint32_t spec_cap;
+  uint32_t serial;       // unmerged rows run from their resolved start (no slot maps)
 };
 
 // The launch plan of one scan (parem_api.cu).
@@ -60,5 +84,9 @@ cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStre
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class_wide(const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s);
+
+cudaError_t launch_batch_scan(const BatchParams& bp, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_emit(const BatchParams& bp, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_tiny(const BatchParams& bp, const uint32_t* tiny_items, uint32_t n_tiny, cudaStream_t s);
 
 }  // namespace parem

@@ -96,7 +96,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   const uint64_t o_segrec = up256(o_status + pl.n_chunks * 8);
   const uint64_t o_rows = up256(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0));
   const uint64_t o_slot = up256(o_rows + (emit ? pl.R * kRowSlotBytes : 0));
-  const uint64_t slot_bytes = pl.R * (uint64_t)pl.cand_stride * 4;
+  const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
   const uint64_t total = up256(o_slot + 2 * slot_bytes);
   if (total > PAREM_NOALLOC_SCRATCH_BYTES) return PAREM_ERR_TOO_LARGE;
   uint8_t* sb = static_cast<uint8_t*>(area);
@@ -121,6 +121,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   p.enum_all = 0;
   p.spec_cap = pl.spec_cap;
   p.cand_stride = pl.cand_stride;
+  p.serial_fallback = pl.serial;
   p.wait_budget = 4000000000ull;
   p.skip_publish = -1;
   p.ticket = reinterpret_cast<uint32_t*>(sb);

@@ -47,6 +47,56 @@ uint32_t row_pitch(uint32_t cols, uint32_t esize) {
 
 }  // namespace
 
+// How many symbols a speculative candidate set needs before it shrinks to one state, for the
+// planner's row length: median over 5 seeded trials, each starting from the candidate set of
+// a random live class and driven by live classes drawn uniformly (splitmix64).  A trial that
+// has not synchronised when its work (the sum of the set sizes) reaches 2^24 gives kNoSync.
+uint32_t estimate_sync(const std::vector<std::vector<uint32_t>>& cols, const Prepared& P) {
+  std::vector<uint32_t> live;
+  for (uint32_t c = 0; c < P.n_classes; ++c)
+    if (P.img_off[c + 1] - P.img_off[c] > 0) live.push_back(c);
+  if (live.empty() || P.max_cand <= 1) return 0;
+  uint64_t x = 0x9E3779B97F4A7C15ull ^ P.n;
+  auto next_rand = [&x]() {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  std::vector<uint32_t> res;
+  std::vector<uint32_t> cur, nxt;
+  std::vector<uint32_t> mark(P.n, 0);
+  uint32_t stamp = 0;
+  for (int trial = 0; trial < 5; ++trial) {
+    const uint32_t c0 = live[next_rand() % live.size()];
+    cur.assign(P.img.begin() + P.img_off[c0], P.img.begin() + P.img_off[c0 + 1]);
+    uint64_t work = 0;
+    uint32_t t = 0;
+    bool sync = true;
+    while (cur.size() > 1) {
+      if (work > (1ull << 24)) {
+        sync = false;
+        break;
+      }
+      const uint32_t c = live[next_rand() % live.size()];
+      ++stamp;
+      nxt.clear();
+      for (uint32_t q : cur) {
+        const uint32_t r = cols[c][q];
+        if (r == P.dead || mark[r] == stamp) continue;
+        mark[r] = stamp;
+        nxt.push_back(r);
+      }
+      work += cur.size();
+      cur.swap(nxt);
+      ++t;
+    }
+    res.push_back(sync ? t : kNoSync);
+  }
+  std::sort(res.begin(), res.end());
+  return res[res.size() / 2];
+}
+
 int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
                 const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
                 uint32_t smem_table_budget, Prepared* out) {
@@ -233,6 +283,7 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
     tot += P.img_off[c + 1] - P.img_off[c];
   }
   P.mean_cand = tot / 256.0;
+  P.sync_len = estimate_sync(cols, P);
   if (P.img.empty()) P.img.push_back(0);
   *out = std::move(P);
   return PAREM_OK;

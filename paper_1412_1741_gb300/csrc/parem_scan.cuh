@@ -111,6 +111,23 @@ __device__ __forceinline__ uint32_t read_error(const DevResult* r) {
   return *reinterpret_cast<const volatile uint32_t*>(&r->error);
 }
 
+__device__ __forceinline__ uint32_t read_progress(const DevResult* r) {
+  return *reinterpret_cast<const volatile uint32_t*>(&r->progress);
+}
+
+// A device wait gives up when its budget has passed with no serial progress anywhere in the
+// scan: *t0 and *seen restart while the progress word moves.
+__device__ __forceinline__ bool wait_expired(const DevResult* r, uint64_t budget, long long* t0, uint32_t* seen) {
+  if ((uint64_t)(clock64() - *t0) <= budget) return false;
+  const uint32_t pr = read_progress(r);
+  if (pr != *seen) {
+    *seen = pr;
+    *t0 = clock64();
+    return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------------------
 // Transition table access.  The column map sits at shared offset 0 and the table (shared
 // layouts) at kTableOff, both addressed from the dynamic shared base, so a lookup is one
@@ -120,10 +137,12 @@ template <int LAYOUT, int ESIZE>
 struct Tab {
   static constexpr bool kByte = LAYOUT == kByteSmem;
   static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW;
-  static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW;
+  static constexpr bool kDyn = LAYOUT == kBatchDyn;
+  static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW || LAYOUT == kBatchDyn;
   const uint8_t* sm;       // dynamic shared memory base
   const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
+  uint32_t smem_tier;      // kBatchDyn: 1 when the table is staged in shared memory
 
   __device__ __forceinline__ uint32_t col(uint32_t b) const {
     if (kByte) return b * ESIZE;
@@ -132,7 +151,7 @@ struct Tab {
   }
   __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
     const uint32_t o = s * rowbytes + c;
-    if (kGlobal) {
+    if (kGlobal || (kDyn && !smem_tier)) {
       return ESIZE == 1 ? (uint32_t)__ldg(gtable + o)
                         : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(gtable + o));
     }
@@ -155,6 +174,18 @@ __device__ __forceinline__ void load_tables(uint8_t* sm, const DeviceDfa& D) {
   }
 }
 
+// Batch kernels: the column map, and the table when it is staged, of one slot's DFA.
+__device__ __forceinline__ void load_tables_dyn(uint8_t* sm, const DeviceDfa& D, uint32_t smem_tier) {
+  const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
+  uint4* dst = reinterpret_cast<uint4*>(sm);
+  for (uint32_t i = threadIdx.x; i < 512 / 16; i += blockDim.x) dst[i] = src[i];
+  if (smem_tier) {
+    const uint4* ts = reinterpret_cast<const uint4*>(D.table);
+    uint4* td = reinterpret_cast<uint4*>(sm + kTableOff);
+    for (uint32_t i = threadIdx.x; i < D.table_bytes / 16; i += blockDim.x) td[i] = ts[i];
+  }
+}
+
 // Run [0, len) of a 16-byte aligned global range from state x.  Adds the matches to *cnt
 // and returns the end state; stops early (returning dead) once the run is dead.
 template <int LAYOUT, int ESIZE>
@@ -171,6 +202,39 @@ __device__ uint32_t run_range16(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p,
     if (x == dead) break;
   }
   // a dead run cannot have counted matches after dying (dead < first_accept)
+  *cnt += c;
+  return x;
+}
+
+// The whole warp runs one state chain x (warp-uniform) over a 16-byte aligned global range
+// [0, len): the lanes load the next 512 bytes while the current 512 are consumed from
+// registers by shuffles.  Returns the (uniform) end state; adds the matches to *cnt.
+template <int LAYOUT, int ESIZE>
+__device__ uint32_t warp_run_range16(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p, uint64_t len,
+                                     uint32_t x, uint32_t dead, uint32_t first_accept, uint32_t* cnt,
+                                     uint32_t lane) {
+  uint32_t c = 0;
+  const uint4 zero = make_uint4(0, 0, 0, 0);
+  uint4 cur = (uint64_t)lane * 16 < len ? ldg16(p + lane * 16) : zero;
+  for (uint64_t base = 0; base < len && x != dead; base += 512) {
+    const uint64_t nb = base + 512 + (uint64_t)lane * 16;
+    const uint4 nxt = nb < len ? ldg16(p + nb) : zero;
+    const uint64_t left16 = (len - base) / 16;
+    const uint32_t nv = left16 < 32 ? (uint32_t)left16 : 32u;
+    for (uint32_t k = 0; k < nv; ++k) {
+      uint4 v;
+      v.x = __shfl_sync(kFull, cur.x, k);
+      v.y = __shfl_sync(kFull, cur.y, k);
+      v.z = __shfl_sync(kFull, cur.z, k);
+      v.w = __shfl_sync(kFull, cur.w, k);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        x = tab.next(x, tab.col(byte_of(v, i)));
+        c += (x >= first_accept);
+      }
+    }
+    cur = nxt;
+  }
   *cnt += c;
   return x;
 }
@@ -226,531 +290,528 @@ __device__ __forceinline__ uint32_t stage_region_off(const uint8_t* smem_raw, ui
   return ((a + 1023u) & ~1023u) - base;
 }
 
-// ---------------------------------------------------------------------------------------
-// Pass 1: speculation, main run, look-back.  P = candidate registers per lane when one row
-// is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
-// ---------------------------------------------------------------------------------------
-template <int LAYOUT, int ESIZE, int P>
-__global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
-    k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  uint8_t* const sm = smem_raw;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const DeviceDfa& D = p.dfa;
-  load_tables<LAYOUT, ESIZE>(sm, D);
-  const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
-  const uint32_t stage0 = region + warp * (kStages * kStageBytes);
-  const uint32_t bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
-  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * p.spec_bytes;
-  uint16_t* hand = reinterpret_cast<uint16_t*>(sm + spec0);
-  uint32_t* cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
-  // 2 x bitmap_words words of candidate bitmaps, then a list of up to 256 states
-  uint32_t* bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
-  if (lane == 0) {
-    for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + bar0 + 8 * s), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
+// Per-warp state of pass 1 that persists from chunk to chunk.
+struct WarpCtx {
+  uint8_t* sm;          // dynamic shared memory base
+  uint32_t lane;
+  uint32_t stage0;      // offset of this warp's TMA stages
+  uint32_t bar0;        // offset of this warp's stage barriers
+  uint16_t* hand;       // hand-over lists (32 rows x 8 states)
+  uint32_t* cbuf;       // compaction buffer (32 words)
+  uint32_t* bitmaps;    // candidate bitmaps and state list (bitmap phase)
+  uint32_t phase_bits;  // expected parity of each stage barrier
+  uint32_t pending;     // stages issued and not yet waited
+};
 
-  Tab<LAYOUT, ESIZE> tab;
-  tab.sm = sm;
-  tab.gtable = D.table;
-  tab.rowbytes = D.rowbytes;
+// One chunk (32 rows) of one text: speculation, main run, look-back, row records.
+template <int LAYOUT, int ESIZE, int P>
+__device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p,
+                                           const CUtensorMap* tmap, const uint64_t j) {
+  uint8_t* const sm = wc.sm;
+  const uint32_t lane = wc.lane, stage0 = wc.stage0, bar0 = wc.bar0;
+  uint16_t* const hand = wc.hand;
+  uint32_t* const cbuf = wc.cbuf;
+  uint32_t* const bitmaps = wc.bitmaps;
+  uint32_t& phase_bits = wc.phase_bits;
+  uint32_t& pending = wc.pending;
+  const DeviceDfa& D = p.dfa;
   const uint32_t dead = D.dead;  // kEmpty when the DFA has no dead state
   const uint32_t A = D.first_accept;
   const uint32_t nblk = (uint32_t)(p.S / kBox);
   const uint32_t issue_first = nblk < kStages ? nblk : kStages;
   const uint32_t cap = p.spec_cap;
   const unsigned lt_mask = (1u << lane) - 1u;
-  uint32_t phase_bits = 0;  // expected parity of each stage barrier
-  uint32_t pending = 0;     // stages issued and not yet waited
+  const uint64_t row0 = j * kLanes;
+  const uint64_t myrow = row0 + lane;
+  const bool active = myrow < p.R;
+  const uint32_t nrows = (uint32_t)((p.R - row0) < kLanes ? (p.R - row0) : kLanes);
+  const uint8_t* body = p.text + p.h;  // 16-byte aligned
+  const bool last_row = active && myrow == p.R - 1;
+  const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
 
-  for (;;) {
-    uint32_t ticket = 0;
-    if (lane == 0) ticket = read_error(p.result) ? 0xFFFFFFFFu : atomicAdd(p.ticket, 1u);
-    ticket = __shfl_sync(kFull, ticket, 0);
-    if ((uint64_t)ticket >= p.n_chunks) break;
-    const uint64_t j = ticket;
-    const uint64_t row0 = j * kLanes;
-    const uint64_t myrow = row0 + lane;
-    const bool active = myrow < p.R;
-    const uint32_t nrows = (uint32_t)((p.R - row0) < kLanes ? (p.R - row0) : kLanes);
-    const uint8_t* body = p.text + p.h;  // 16-byte aligned
-    const bool last_row = active && myrow == p.R - 1;
-    const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
-
-    // 1. start the TMA pipeline for this chunk
-    if (lane == 0) {
-      for (uint32_t b = 0; b < issue_first; ++b) {
-        const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
-        mbar_arrive_expect_tx(bar, kStageBytes);
-        tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), &tmap, bar, (int32_t)(b * kBox),
-                    (int32_t)row0);
-      }
+  // 1. start the TMA pipeline for this chunk
+  if (lane == 0) {
+    for (uint32_t b = 0; b < issue_first; ++b) {
+      const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
+      mbar_arrive_expect_tx(bar, kStageBytes);
+      tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), tmap, bar, (int32_t)(b * kBox),
+                  (int32_t)row0);
     }
-    pending |= (1u << issue_first) - 1u;
-    bool failed = false;
-    for (uint32_t b = 0; b < issue_first && !failed; ++b) {
-      if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
-        set_error(p.result, kErrTimeout);
-        failed = true;
-      }
+  }
+  pending |= (1u << issue_first) - 1u;
+  bool failed = false;
+  for (uint32_t b = 0; b < issue_first && !failed; ++b) {
+    if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
+      set_error(p.result, kErrTimeout);
+      failed = true;
     }
-    // 16 bytes of row k of this chunk at row offset pos (staged bytes from shared memory)
-    auto read16 = [&](uint32_t k, uint32_t pos) -> uint4 {
-      if (pos < issue_first * kBox) {
-        const uint32_t b = pos / kBox;
-        const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
-        return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
-      }
-      return ldg16(body + (row0 + k) * p.S + pos);
-    };
-    auto cand_class = [&](uint64_t r) -> uint32_t {
-      return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
-    };
+  }
+  // 16 bytes of row k of this chunk at row offset pos (staged bytes from shared memory)
+  auto read16 = [&](uint32_t k, uint32_t pos) -> uint4 {
+    if (pos < issue_first * kBox) {
+      const uint32_t b = pos / kBox;
+      const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
+      return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
+    }
+    return ldg16(body + (row0 + k) * p.S + pos);
+  };
+  auto cand_class = [&](uint64_t r) -> uint32_t {
+    return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
+  };
 
-    uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
-    if constexpr (P == 1) {
-      // 2. grouped speculation: G lanes per row, 32/G rows per pass
-      const uint32_t G = p.group;
-      const uint32_t rpp = kLanes / G;
-      const uint32_t gi = lane / G, gl = lane % G;
-      const unsigned gmask = (G == 32u) ? kFull : (((1u << G) - 1u) << (gi * G));
-      for (uint32_t k0 = 0; k0 < nrows && !failed; k0 += rpp) {
-        const uint32_t k = k0 + gi;
-        const bool valid = k < nrows;
-        const uint64_t r = row0 + k;
-        uint32_t st = kEmpty, hc = 0;
-        bool exact = false;
-        if (valid) {
-          if (r == 0) {
-            // row 0 starts from the exact state: the initial state run over the head bytes
-            if (gl == 0) {
-              st = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &hc);
-              if (st == dead) st = kEmpty;
-            }
-            exact = true;
-          } else {
-            const uint32_t cls = cand_class(r);
-            const uint32_t off = D.img_off[cls];
-            const uint32_t m = D.img_off[cls + 1] - off;
-            if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
-          }
-        }
-        // a row whose group has at most one live lane is already merged at t = 0
-        unsigned live = __ballot_sync(kFull, st != kEmpty);
-        bool done = exact || !valid || __popc(live & gmask) <= 1;
-        uint32_t pos = 0, outcome = 1;
-        while (!__all_sync(kFull, done)) {
-          if (!done && pos >= cap) {
-            done = true;
-            outcome = 3;
-          }
-          const uint4 v = read16(valid ? k : 0u, pos);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-#pragma unroll
-            for (int i2 = 0; i2 < 4; ++i2) {
-              if (!done && st != kEmpty) {
-                const uint32_t s2 = tab.next(st, tab.col(byte_of(v, q * 4 + i2)));
-                st = (s2 == dead) ? kEmpty : s2;
-              }
-            }
-            const uint32_t key = st == kEmpty ? kEmpty : ((gi << 16) | st);
-            const unsigned grp = __match_any_sync(kFull, key);
-            if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
-          }
-          if (!done) pos += 16;
-          live = __ballot_sync(kFull, st != kEmpty);
-          if (!done && __popc(live & gmask) <= 1) done = true;
-        }
-        // the surviving state of each row (or dead) and the outcome go to the row's lane
-        live = __ballot_sync(kFull, st != kEmpty);
-        const unsigned mine = live & gmask;
-        const uint32_t sig = __shfl_sync(kFull, st, mine ? (uint32_t)(__ffs(mine) - 1) : gi * G);
-        const uint32_t sigma_row = mine ? sig : dead;
-        const uint32_t hcg = __shfl_sync(kFull, hc, gi * G);
-        // lane k (k in [k0, k0 + rpp)) collects from group k - k0
-        const uint32_t from = ((lane - k0) % rpp) * G;
-        const uint32_t o_sig = __shfl_sync(kFull, sigma_row, from);
-        const uint32_t o_out = __shfl_sync(kFull, outcome, from);
-        const uint32_t o_pos = __shfl_sync(kFull, pos, from);
-        const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
-        if (lane >= k0 && lane < k0 + rpp && lane < nrows) {
-          my_conv = o_out == 1;
-          my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
-          my_sigma = o_out == 1 ? o_sig : kEmpty;
-          head_cnt = o_hc;
-        }
-      }
-      if (row0 != 0 || lane != 0) head_cnt = 0;
-    } else {
-      // 2a. warp-wide speculation, one row at a time, candidates across lanes and registers
-      for (uint32_t k = 0; k < nrows && !failed; ++k) {
-        const uint64_t r = row0 + k;
+  uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
+  if constexpr (P == 1) {
+    // 2. grouped speculation: G lanes per row, 32/G rows per pass
+    const uint32_t G = p.group;
+    const uint32_t rpp = kLanes / G;
+    const uint32_t gi = lane / G, gl = lane % G;
+    const unsigned gmask = (G == 32u) ? kFull : (((1u << G) - 1u) << (gi * G));
+    for (uint32_t k0 = 0; k0 < nrows && !failed; k0 += rpp) {
+      const uint32_t k = k0 + gi;
+      const bool valid = k < nrows;
+      const uint64_t r = row0 + k;
+      uint32_t st = kEmpty, hc = 0;
+      bool exact = false;
+      if (valid) {
         if (r == 0) {
-          uint32_t c0 = 0;
-          const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
-          if (lane == 0) {
-            my_t = 0;
-            my_sigma = sh;
-            head_cnt = c0;
+          // row 0 starts from the exact state: the initial state run over the head bytes
+          if (gl == 0) {
+            st = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &hc);
+            if (st == dead) st = kEmpty;
           }
-          continue;
-        }
-        const uint32_t cls = cand_class(r);
-        const uint32_t off = D.img_off[cls];
-        const uint32_t m = D.img_off[cls + 1] - off;
-        const bool big = m > 32u * P;
-        if (m <= 1 || (big && p.bitmap_words == 0)) {
-          if (lane == k) {
-            my_t = big ? (uint32_t)p.S : 0u;
-            my_conv = m <= 1;
-            my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
-          }
-          continue;
-        }
-        uint32_t st[P];
-        uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
-        uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
-        if (big) {
-          // More candidates than registers: the warp keeps the candidate set as a bitmap over
-          // the states (duplicates merge by construction) until it fits 32 * P registers.
-          const uint32_t W = p.bitmap_words;
-          uint32_t* bm0 = bitmaps;
-          uint32_t* bm1 = bitmaps + W;
-          for (uint32_t w = lane; w < W; w += 32) bm0[w] = 0;
-          __syncwarp();
-          for (uint32_t slot = lane; slot < m; slot += 32) {
-            const uint32_t q = D.img[off + slot];
-            atomicOr(&bm0[q >> 5], 1u << (q & 31u));
-          }
-          __syncwarp();
-          uint32_t cnt = m;
-          for (;;) {
-            if (pos >= cap) {
-              outcome = 3;
-              break;
-            }
-            const uint4 v = read16(k, pos);
-#pragma unroll 1
-            for (int q = 0; q < 16; ++q) {
-              const uint32_t c = tab.col(byte_of(v, q));
-              for (uint32_t w = lane; w < W; w += 32) bm1[w] = 0;
-              __syncwarp();
-              for (uint32_t w = lane; w < W; w += 32) {
-                uint32_t bits = bm0[w];
-                while (bits) {
-                  // up to four independent lookups in flight
-                  uint32_t qs[4], nq[4];
-                  int nb = 0;
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) {
-                    qs[u] = kEmpty;
-                    if (bits) {
-                      qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
-                      bits &= bits - 1;
-                      ++nb;
-                    }
-                  }
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) nq[u] = qs[u] != kEmpty ? tab.next(qs[u], c) : dead;
-#pragma unroll
-                  for (int u = 0; u < 4; ++u)
-                    if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
-                  (void)nb;
-                }
-              }
-              __syncwarp();
-              uint32_t* tmp = bm0;
-              bm0 = bm1;
-              bm1 = tmp;
-            }
-            pos += 16;
-            uint32_t local = 0;
-            for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
-            cnt = __reduce_add_sync(kFull, local);
-            if (cnt <= 32u * P) break;
-          }
-          if (outcome == 0) {
-            // list the surviving states in the hand-over buffer, then load the registers
-            uint32_t local = 0;
-            for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
-            uint32_t incl = local;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-              const uint32_t o = __shfl_up_sync(kFull, incl, d);
-              if (lane >= (uint32_t)d) incl += o;
-            }
-            uint32_t idx = incl - local;
-            // the list has its own buffer after the two bitmaps: the hand-over lists of
-            // earlier rows of this chunk must survive until phase 2b
-            uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
-            for (uint32_t w = lane; w < W; w += 32) {
-              uint32_t bits = bm0[w];
-              while (bits) {
-                list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
-                bits &= bits - 1;
-              }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              const uint32_t slot = (uint32_t)i * 32u + lane;
-              st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
-              if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
-            }
-            __syncwarp();
-          }
+          exact = true;
         } else {
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const uint32_t slot = (uint32_t)i * 32u + lane;
-            st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
-            if ((uint32_t)i * 32u < m) lr |= 1u << i;
-          }
+          const uint32_t cls = cand_class(r);
+          const uint32_t off = D.img_off[cls];
+          const uint32_t m = D.img_off[cls + 1] - off;
+          if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
         }
-        for (; outcome == 0;) {
+      }
+      // a row whose group has at most one live lane is already merged at t = 0
+      unsigned live = __ballot_sync(kFull, st != kEmpty);
+      bool done = exact || !valid || __popc(live & gmask) <= 1;
+      uint32_t pos = 0, outcome = 1;
+      while (!__all_sync(kFull, done)) {
+        if (!done && pos >= cap) {
+          done = true;
+          outcome = 3;
+        }
+        const uint4 v = read16(valid ? k : 0u, pos);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int i2 = 0; i2 < 4; ++i2) {
+            if (!done && st != kEmpty) {
+              const uint32_t s2 = tab.next(st, tab.col(byte_of(v, q * 4 + i2)));
+              st = (s2 == dead) ? kEmpty : s2;
+            }
+          }
+          const uint32_t key = st == kEmpty ? kEmpty : ((gi << 16) | st);
+          const unsigned grp = __match_any_sync(kFull, key);
+          if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
+        }
+        if (!done) pos += 16;
+        live = __ballot_sync(kFull, st != kEmpty);
+        if (!done && __popc(live & gmask) <= 1) done = true;
+      }
+      // the surviving state of each row (or dead) and the outcome go to the row's lane
+      live = __ballot_sync(kFull, st != kEmpty);
+      const unsigned mine = live & gmask;
+      const uint32_t sig = __shfl_sync(kFull, st, mine ? (uint32_t)(__ffs(mine) - 1) : gi * G);
+      const uint32_t sigma_row = mine ? sig : dead;
+      const uint32_t hcg = __shfl_sync(kFull, hc, gi * G);
+      // lane k (k in [k0, k0 + rpp)) collects from group k - k0
+      const uint32_t from = ((lane - k0) % rpp) * G;
+      const uint32_t o_sig = __shfl_sync(kFull, sigma_row, from);
+      const uint32_t o_out = __shfl_sync(kFull, outcome, from);
+      const uint32_t o_pos = __shfl_sync(kFull, pos, from);
+      const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
+      if (lane >= k0 && lane < k0 + rpp && lane < nrows) {
+        my_conv = o_out == 1;
+        my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
+        my_sigma = o_out == 1 ? o_sig : kEmpty;
+        head_cnt = o_hc;
+      }
+    }
+    if (row0 != 0 || lane != 0) head_cnt = 0;
+  } else {
+    // 2a. warp-wide speculation, one row at a time, candidates across lanes and registers
+    for (uint32_t k = 0; k < nrows && !failed; ++k) {
+      const uint64_t r = row0 + k;
+      if (r == 0) {
+        uint32_t c0 = 0;
+        const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
+        if (lane == 0) {
+          my_t = 0;
+          my_sigma = sh;
+          head_cnt = c0;
+        }
+        continue;
+      }
+      const uint32_t cls = cand_class(r);
+      const uint32_t off = D.img_off[cls];
+      const uint32_t m = D.img_off[cls + 1] - off;
+      const bool big = m > 32u * P;
+      if (m <= 1 || (big && p.bitmap_words == 0)) {
+        if (lane == k) {
+          my_t = big ? (uint32_t)p.S : 0u;
+          my_conv = m <= 1;
+          my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
+        }
+        continue;
+      }
+      uint32_t st[P];
+      uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
+      uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
+      if (big) {
+        // More candidates than registers: the warp keeps the candidate set as a bitmap over
+        // the states (duplicates merge by construction) until it fits 32 * P registers.
+        const uint32_t W = p.bitmap_words;
+        uint32_t* bm0 = bitmaps;
+        uint32_t* bm1 = bitmaps + W;
+        for (uint32_t w = lane; w < W; w += 32) bm0[w] = 0;
+        __syncwarp();
+        for (uint32_t slot = lane; slot < m; slot += 32) {
+          const uint32_t q = D.img[off + slot];
+          atomicOr(&bm0[q >> 5], 1u << (q & 31u));
+        }
+        __syncwarp();
+        uint32_t cnt = m;
+        for (;;) {
           if (pos >= cap) {
             outcome = 3;
             break;
           }
           const uint4 v = read16(k, pos);
+#pragma unroll 1
+          for (int q = 0; q < 16; ++q) {
+            const uint32_t c = tab.col(byte_of(v, q));
+            for (uint32_t w = lane; w < W; w += 32) bm1[w] = 0;
+            __syncwarp();
+            for (uint32_t w = lane; w < W; w += 32) {
+              uint32_t bits = bm0[w];
+              while (bits) {
+                // up to four independent lookups in flight
+                uint32_t qs[4], nq[4];
+                int nb = 0;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-#pragma unroll
-            for (int i2 = 0; i2 < 4; ++i2) {
-              const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
-#pragma unroll
-              for (int i = 0; i < P; ++i) {
-                if ((lr >> i) & 1u) {
-                  if (st[i] != kEmpty) {
-                    const uint32_t s2 = tab.next(st[i], c);
-                    st[i] = (s2 == dead) ? kEmpty : s2;
+                for (int u = 0; u < 4; ++u) {
+                  qs[u] = kEmpty;
+                  if (bits) {
+                    qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
+                    bits &= bits - 1;
+                    ++nb;
                   }
                 }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) nq[u] = qs[u] != kEmpty ? tab.next(qs[u], c) : dead;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
+                (void)nb;
               }
             }
-            // merge lanes whose candidates met (within each register)
+            __syncwarp();
+            uint32_t* tmp = bm0;
+            bm0 = bm1;
+            bm1 = tmp;
+          }
+          pos += 16;
+          uint32_t local = 0;
+          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+          cnt = __reduce_add_sync(kFull, local);
+          if (cnt <= 32u * P) break;
+        }
+        if (outcome == 0) {
+          // list the surviving states in the hand-over buffer, then load the registers
+          uint32_t local = 0;
+          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+          uint32_t incl = local;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += o;
+          }
+          uint32_t idx = incl - local;
+          // the list has its own buffer after the two bitmaps: the hand-over lists of
+          // earlier rows of this chunk must survive until phase 2b
+          uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
+          for (uint32_t w = lane; w < W; w += 32) {
+            uint32_t bits = bm0[w];
+            while (bits) {
+              list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
+              bits &= bits - 1;
+            }
+          }
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const uint32_t slot = (uint32_t)i * 32u + lane;
+            st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
+            if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
+          }
+          __syncwarp();
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const uint32_t slot = (uint32_t)i * 32u + lane;
+          st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
+          if ((uint32_t)i * 32u < m) lr |= 1u << i;
+        }
+      }
+      for (; outcome == 0;) {
+        if (pos >= cap) {
+          outcome = 3;
+          break;
+        }
+        const uint4 v = read16(k, pos);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int i2 = 0; i2 < 4; ++i2) {
+            const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
 #pragma unroll
             for (int i = 0; i < P; ++i) {
               if ((lr >> i) & 1u) {
-                const unsigned grp = __match_any_sync(kFull, st[i]);
-                if (st[i] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[i] = kEmpty;
+                if (st[i] != kEmpty) {
+                  const uint32_t s2 = tab.next(st[i], c);
+                  st[i] = (s2 == dead) ? kEmpty : s2;
+                }
+              }
+            }
+          }
+          // merge lanes whose candidates met (within each register)
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            if ((lr >> i) & 1u) {
+              const unsigned grp = __match_any_sync(kFull, st[i]);
+              if (st[i] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[i] = kEmpty;
+            }
+          }
+        }
+        pos += 16;
+        uint32_t total = 0, nlr = 0;
+        unsigned bl[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          bl[i] = ((lr >> i) & 1u) ? __ballot_sync(kFull, st[i] != kEmpty) : 0u;
+          total += __popc(bl[i]);
+          if (bl[i]) nlr |= 1u << i;
+        }
+        lr = nlr;
+        if (total <= 32 && (lr & ~1u)) {
+          // all survivors fit one register: compact them into register 0, then merge
+          uint32_t base = 0;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            if (st[i] != kEmpty) cbuf[base + __popc(bl[i] & lt_mask)] = st[i];
+            base += __popc(bl[i]);
+          }
+          __syncwarp();
+          st[0] = lane < total ? cbuf[lane] : kEmpty;
+#pragma unroll
+          for (int i = 1; i < P; ++i) st[i] = kEmpty;
+          __syncwarp();
+          const unsigned grp = __match_any_sync(kFull, st[0]);
+          if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
+          bl[0] = __ballot_sync(kFull, st[0] != kEmpty);
+#pragma unroll
+          for (int i = 1; i < P; ++i) bl[i] = 0;
+          total = __popc(bl[0]);
+          lr = 1;
+        }
+        if (total <= 1) {
+          outcome = 1;
+          if (total == 0) {
+            sigma = dead;
+          } else {
+            uint32_t reg = 0, holder = 0;
+#pragma unroll
+            for (int i = P - 1; i >= 0; --i)
+              if (bl[i]) {
+                reg = (uint32_t)i;
+                holder = __ffs(bl[i]) - 1;
+              }
+            uint32_t val = kEmpty;
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+              if ((uint32_t)i == reg) val = st[i];
+            sigma = __shfl_sync(kFull, val, holder);
+          }
+          break;
+        }
+        if (total <= kLaneCand && lr == 1u) {
+          // few survivors left: the lane that owns the row finishes them (phase 2b)
+          if (st[0] != kEmpty) hand[k * kLaneCand + __popc(bl[0] & lt_mask)] = (uint16_t)st[0];
+          sigma = total;
+          outcome = 2;
+          break;
+        }
+      }
+      if (lane == k) {
+        my_conv = outcome == 1;
+        my_t = outcome == 3 ? (uint32_t)p.S : pos;
+        my_sigma = outcome == 1 ? sigma : kEmpty;
+        my_hand = outcome == 2 ? sigma : 0u;
+      }
+    }
+
+    // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
+    if (__ballot_sync(kFull, my_hand != 0) && !failed) {
+      __syncwarp();
+      if (my_hand) {
+        uint32_t ls[kLaneCand];
+#pragma unroll
+        for (uint32_t i = 0; i < kLaneCand; ++i)
+          ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
+        uint32_t L = my_hand, pos = my_t;
+        for (;;) {
+          if (pos >= cap) {
+            my_conv = 0;
+            my_t = (uint32_t)p.S;
+            break;
+          }
+          const uint4 v = read16(lane, pos);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const uint32_t c = tab.col(byte_of(v, q));
+#pragma unroll
+            for (uint32_t i = 0; i < kLaneCand; ++i) {
+              if (i < L && ls[i] != kEmpty) {
+                const uint32_t s2 = tab.next(ls[i], c);
+                ls[i] = (s2 == dead) ? kEmpty : s2;
               }
             }
           }
           pos += 16;
-          uint32_t total = 0, nlr = 0;
-          unsigned bl[P];
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            bl[i] = ((lr >> i) & 1u) ? __ballot_sync(kFull, st[i] != kEmpty) : 0u;
-            total += __popc(bl[i]);
-            if (bl[i]) nlr |= 1u << i;
-          }
-          lr = nlr;
-          if (total <= 32 && (lr & ~1u)) {
-            // all survivors fit one register: compact them into register 0, then merge
-            uint32_t base = 0;
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              if (st[i] != kEmpty) cbuf[base + __popc(bl[i] & lt_mask)] = st[i];
-              base += __popc(bl[i]);
-            }
-            __syncwarp();
-            st[0] = lane < total ? cbuf[lane] : kEmpty;
-#pragma unroll
-            for (int i = 1; i < P; ++i) st[i] = kEmpty;
-            __syncwarp();
-            const unsigned grp = __match_any_sync(kFull, st[0]);
-            if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
-            bl[0] = __ballot_sync(kFull, st[0] != kEmpty);
-#pragma unroll
-            for (int i = 1; i < P; ++i) bl[i] = 0;
-            total = __popc(bl[0]);
-            lr = 1;
-          }
-          if (total <= 1) {
-            outcome = 1;
-            if (total == 0) {
-              sigma = dead;
-            } else {
-              uint32_t reg = 0, holder = 0;
-#pragma unroll
-              for (int i = P - 1; i >= 0; --i)
-                if (bl[i]) {
-                  reg = (uint32_t)i;
-                  holder = __ffs(bl[i]) - 1;
-                }
-              uint32_t val = kEmpty;
-#pragma unroll
-              for (int i = 0; i < P; ++i)
-                if ((uint32_t)i == reg) val = st[i];
-              sigma = __shfl_sync(kFull, val, holder);
-            }
-            break;
-          }
-          if (total <= kLaneCand && lr == 1u) {
-            // few survivors left: the lane that owns the row finishes them (phase 2b)
-            if (st[0] != kEmpty) hand[k * kLaneCand + __popc(bl[0] & lt_mask)] = (uint16_t)st[0];
-            sigma = total;
-            outcome = 2;
-            break;
-          }
-        }
-        if (lane == k) {
-          my_conv = outcome == 1;
-          my_t = outcome == 3 ? (uint32_t)p.S : pos;
-          my_sigma = outcome == 1 ? sigma : kEmpty;
-          my_hand = outcome == 2 ? sigma : 0u;
-        }
-      }
-
-      // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
-      if (__ballot_sync(kFull, my_hand != 0) && !failed) {
-        __syncwarp();
-        if (my_hand) {
-          uint32_t ls[kLaneCand];
 #pragma unroll
           for (uint32_t i = 0; i < kLaneCand; ++i)
-            ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
-          uint32_t L = my_hand, pos = my_t;
-          for (;;) {
-            if (pos >= cap) {
-              my_conv = 0;
-              my_t = (uint32_t)p.S;
-              break;
-            }
-            const uint4 v = read16(lane, pos);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const uint32_t c = tab.col(byte_of(v, q));
+            for (uint32_t jj = i + 1; jj < kLaneCand; ++jj)
+              if (ls[jj] == ls[i]) ls[jj] = kEmpty;
+          uint32_t out[kLaneCand];
 #pragma unroll
-              for (uint32_t i = 0; i < kLaneCand; ++i) {
-                if (i < L && ls[i] != kEmpty) {
-                  const uint32_t s2 = tab.next(ls[i], c);
-                  ls[i] = (s2 == dead) ? kEmpty : s2;
-                }
-              }
-            }
-            pos += 16;
+          for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
+          uint32_t np = 0;
 #pragma unroll
-            for (uint32_t i = 0; i < kLaneCand; ++i)
+          for (uint32_t i = 0; i < kLaneCand; ++i) {
+            const bool keep = ls[i] != kEmpty;
 #pragma unroll
-              for (uint32_t jj = i + 1; jj < kLaneCand; ++jj)
-                if (ls[jj] == ls[i]) ls[jj] = kEmpty;
-            uint32_t out[kLaneCand];
-#pragma unroll
-            for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
-            uint32_t np = 0;
-#pragma unroll
-            for (uint32_t i = 0; i < kLaneCand; ++i) {
-              const bool keep = ls[i] != kEmpty;
-#pragma unroll
-              for (uint32_t qq = 0; qq < kLaneCand; ++qq)
-                if (keep && qq == np) out[qq] = ls[i];
-              np += keep ? 1u : 0u;
-            }
-#pragma unroll
-            for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
-            L = np;
-            if (L <= 1) {
-              my_conv = 1;
-              my_t = pos;
-              my_sigma = L ? ls[0] : dead;
-              break;
-            }
+            for (uint32_t qq = 0; qq < kLaneCand; ++qq)
+              if (keep && qq == np) out[qq] = ls[i];
+            np += keep ? 1u : 0u;
           }
-          my_hand = 0;
-        }
-        __syncwarp();
-      }
-    }
-
-    // 3. slot maps of rows whose candidates did not merge (rare): every candidate runs
-    //    the whole row (and the tail on the last row), lanes over candidates
-    unsigned nonconv = __ballot_sync(kFull, active && !my_conv);
-    while (nonconv && !failed) {
-      const uint32_t k = __ffs(nonconv) - 1;
-      nonconv &= nonconv - 1;
-      const uint64_t r = row0 + k;
-      const uint32_t cls = cand_class(r);
-      const uint32_t off = D.img_off[cls];
-      const uint32_t m = D.img_off[cls + 1] - off;
-      for (uint32_t base = 0; base < m; base += 32) {
-        const uint32_t slot = base + lane;
-        uint32_t x = slot < m ? (uint32_t)D.img[off + slot] : 0u;
-        uint32_t c = 0;
-        x = run_range16(tab, body + r * p.S, p.S, x, dead, A, &c);
-        if (r == p.R - 1 && p.tail) x = run_bytes(tab, body + p.R * p.S, p.tail, x, dead, A, &c);
-        if (slot < m) {
-          p.slot_end[r * p.cand_stride + slot] = x;
-          p.slot_cnt[r * p.cand_stride + slot] = c;
-        }
-      }
-    }
-
-    // 4. main run: each lane runs its merged state over the rest of its row from smem,
-    //    remembering the first and last 16-byte vectors that contain matches
-    uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
-    const bool run = active && my_conv;
-    uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
-    for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
-      const uint32_t b = blk % kStages;
-      const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
-      if (!stage_wait(bar, (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
-        set_error(p.result, kErrTimeout);
-        failed = true;
-        break;
-      }
-      phase_bits ^= 1u << b;
-      pending &= ~(1u << b);
-      uint4 v[kBox / 16];
-      const uint8_t* stg = sm + stage0 + b * kStageBytes + lane * kBox;
 #pragma unroll
-      for (uint32_t i = 0; i < kBox / 16; ++i)
-        v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane >> 1) & 3u)) * 16u));
+          for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
+          L = np;
+          if (L <= 1) {
+            my_conv = 1;
+            my_t = pos;
+            my_sigma = L ? ls[0] : dead;
+            break;
+          }
+        }
+        my_hand = 0;
+      }
       __syncwarp();
-      if (blk + kStages < nblk) {
-        if (lane == 0) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive_expect_tx(bar, kStageBytes);
-          tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), &tmap, bar,
-                      (int32_t)((blk + kStages) * kBox), (int32_t)row0);
-        }
-        pending |= 1u << b;
+    }
+  }
+
+  // convergence statistics for the planner (one update per chunk)
+  {
+    const unsigned nc = __ballot_sync(kFull, active && !my_conv);
+    uint32_t tmax = (active && my_conv) ? my_t : 0u;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) tmax = max(tmax, __shfl_xor_sync(kFull, tmax, d));
+    if (lane == 0) {
+      if (nc) atomicAdd(&p.result->nonconv_rows, (uint32_t)__popc(nc));
+      if (tmax) atomicMax(&p.result->conv_max, tmax);
+    }
+  }
+
+  // 3. slot maps of rows whose candidates did not merge (rare): every candidate runs
+  //    the whole row (and the tail on the last row), lanes over candidates
+  unsigned nonconv = p.serial_fallback ? 0u : __ballot_sync(kFull, active && !my_conv);
+  while (nonconv && !failed) {
+    const uint32_t k = __ffs(nonconv) - 1;
+    nonconv &= nonconv - 1;
+    const uint64_t r = row0 + k;
+    const uint32_t cls = cand_class(r);
+    const uint32_t off = D.img_off[cls];
+    const uint32_t m = D.img_off[cls + 1] - off;
+    for (uint32_t base = 0; base < m; base += 32) {
+      const uint32_t slot = base + lane;
+      uint32_t x = slot < m ? (uint32_t)D.img[off + slot] : 0u;
+      uint32_t c = 0;
+      x = run_range16(tab, body + r * p.S, p.S, x, dead, A, &c);
+      if (r == p.R - 1 && p.tail) x = run_bytes(tab, body + p.R * p.S, p.tail, x, dead, A, &c);
+      if (slot < m) {
+        p.slot_end[r * p.cand_stride + slot] = x;
+        p.slot_cnt[r * p.cand_stride + slot] = c;
       }
-      if (run) {
-        const uint32_t col0 = blk * kBox;
+    }
+    if (lane == 0) atomicAdd(&p.result->progress, 1u);
+  }
+
+  // 4. main run: each lane runs its merged state over the rest of its row from smem,
+  //    remembering the first and last 16-byte vectors that contain matches
+  uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
+  const bool run = active && my_conv;
+  uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
+  for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
+    const uint32_t b = blk % kStages;
+    const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
+    if (!stage_wait(bar, (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
+      set_error(p.result, kErrTimeout);
+      failed = true;
+      break;
+    }
+    phase_bits ^= 1u << b;
+    pending &= ~(1u << b);
+    uint4 v[kBox / 16];
+    const uint8_t* stg = sm + stage0 + b * kStageBytes + lane * kBox;
 #pragma unroll
-        for (uint32_t i = 0; i < kBox / 16; ++i) {
-          const uint32_t col = col0 + i * 16u;
-          if (col >= my_t) {
-            const uint32_t mu0 = mu, s0 = s;
+    for (uint32_t i = 0; i < kBox / 16; ++i)
+      v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane >> 1) & 3u)) * 16u));
+    __syncwarp();
+    if (blk + kStages < nblk) {
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, kStageBytes);
+        tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), tmap, bar,
+                    (int32_t)((blk + kStages) * kBox), (int32_t)row0);
+      }
+      pending |= 1u << b;
+    }
+    if (run) {
+      const uint32_t col0 = blk * kBox;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              s = tab.next(s, tab.col(byte_of(v[i], q)));
-              mu += (s >= A);
+      for (uint32_t i = 0; i < kBox / 16; ++i) {
+        const uint32_t col = col0 + i * 16u;
+        if (col >= my_t) {
+          const uint32_t mu0 = mu, s0 = s;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            s = tab.next(s, tab.col(byte_of(v[i], q)));
+            mu += (s >= A);
+          }
+          if (mu != mu0) {
+            if (fv == kEmpty) {
+              fv = col;
+              fs = s0;
             }
-            if (mu != mu0) {
-              if (fv == kEmpty) {
-                fv = col;
-                fs = s0;
-              }
-              lvv = col;
-              ls = s0;
-              if (myslots != nullptr && nrec < kRowSlots) {
-                // replay this vector to record its match positions (rare for sparse matches)
-                uint32_t x = s0;
+            lvv = col;
+            ls = s0;
+            if (myslots != nullptr && nrec < kRowSlots) {
+              // replay this vector to record its match positions (rare for sparse matches)
+              uint32_t x = s0;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                  x = tab.next(x, tab.col(byte_of(v[i], q)));
-                  if (x >= A) {
-                    if (nrec < kRowSlots) myslots[nrec] = col + (uint32_t)q;
-                    ++nrec;
-                  }
+              for (int q = 0; q < 16; ++q) {
+                x = tab.next(x, tab.col(byte_of(v[i], q)));
+                if (x >= A) {
+                  if (nrec < kRowSlots) myslots[nrec] = col + (uint32_t)q;
+                  ++nrec;
                 }
               }
             }
@@ -758,44 +819,100 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
         }
       }
     }
-    if (failed) continue;
-    lv = (fv == kEmpty) ? 0u : lvv + 16u;
-    if (run && last_row && p.tail) {
-      const uint8_t* tp = body + p.R * p.S;
-      for (uint64_t o = 0; o < p.tail; ++o) {
-        const uint32_t s0 = s;
-        s = tab.next(s, tab.col(ldg8(tp + o)));
-        if (s >= A) {
-          ++mu;
-          if (fv == kEmpty) {
-            fv = (uint32_t)(p.S + o);
-            fs = s0;
-          }
-          lvv = (uint32_t)(p.S + o);
-          ls = s0;
-          lv = lvv + 1;
-          if (myslots != nullptr && nrec < kRowSlots) myslots[nrec] = lvv;
-          ++nrec;
+  }
+  if (failed) return;
+  lv = (fv == kEmpty) ? 0u : lvv + 16u;
+  if (run && last_row && p.tail) {
+    const uint8_t* tp = body + p.R * p.S;
+    for (uint64_t o = 0; o < p.tail; ++o) {
+      const uint32_t s0 = s;
+      s = tab.next(s, tab.col(ldg8(tp + o)));
+      if (s >= A) {
+        ++mu;
+        if (fv == kEmpty) {
+          fv = (uint32_t)(p.S + o);
+          fs = s0;
         }
+        lvv = (uint32_t)(p.S + o);
+        ls = s0;
+        lv = lvv + 1;
+        if (myslots != nullptr && nrec < kRowSlots) myslots[nrec] = lvv;
+        ++nrec;
       }
     }
-    const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
+  }
+  const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
 
-    // 5. the chunk's end state is known now if every row merged
-    const bool fast = __ballot_sync(kFull, active && !my_conv) == 0;
-    const bool skip = (int64_t)j == p.skip_publish;
-    const uint32_t E_last = __shfl_sync(kFull, E, nrows - 1);
-    if (fast && lane == 0 && !skip) st_release(&p.status[j], pack_status(kFlagMapped, 0, E_last, 0));
+  // 5. the chunk's end state is known now if every row merged
+  //    (or if at least its last row did: E_last does not depend on the chunk's start, and
+  //    publishing it now keeps chunks with unmerged rows from forming a chain)
+  const bool fast = __ballot_sync(kFull, active && !my_conv) == 0;
+  const bool skip = (int64_t)j == p.skip_publish;
+  const uint32_t E_last = __shfl_sync(kFull, E, nrows - 1);
+  const bool last_merged = __shfl_sync(kFull, my_conv, nrows - 1) != 0;
+  if (last_merged && lane == 0 && !skip) st_release(&p.status[j], pack_status(kFlagMapped, 0, E_last, 0));
 
-    // rows k >= 1: start = end of row k-1 (fast path), count the merged prefix [0, t)
-    uint32_t x_k = __shfl_up_sync(kFull, E, 1);
-    uint32_t cnt_k = 0, dies_k = 0, pre_k = 0, died_pre = 0;
-    if (fast && active && lane >= 1) {
-      if (x_k == dead) {
+  // rows k >= 1: start = end of row k-1 (fast path), count the merged prefix [0, t)
+  uint32_t x_k = __shfl_up_sync(kFull, E, 1);
+  uint32_t cnt_k = 0, dies_k = 0, pre_k = 0, died_pre = 0;
+  if (fast && active && lane >= 1) {
+    if (x_k == dead) {
+      dies_k = 1;
+      died_pre = 1;
+    } else {
+      const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre_k);
+      if (y == dead) {
         dies_k = 1;
         died_pre = 1;
+        cnt_k = pre_k;
       } else {
-        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre_k);
+        if (y != my_sigma) set_error(p.result, kErrInternal);
+        cnt_k = pre_k + mu;
+        dies_k = (E == dead);
+      }
+    }
+  }
+
+  // 6. start state of the chunk: the end state published by chunk j-1
+  uint32_t s_j = p.init_state;
+  if (j > 0) {
+    unsigned long long w = 0;
+    if (lane == 0) {
+      long long t0 = clock64();
+      uint32_t seen = read_progress(p.result);
+      for (;;) {
+        w = ld_acquire(&p.status[j - 1]);
+        if ((w >> 62) != 0) break;
+        if (read_error(p.result) || wait_expired(p.result, p.wait_budget, &t0, &seen)) {
+          set_error(p.result, kErrTimeout);
+          w = 0;
+          break;
+        }
+      }
+    }
+    w = __shfl_sync(kFull, w, 0);
+    if ((w >> 62) == 0) return;  // failed: the error word is set
+    s_j = (uint32_t)((w >> 45) & 0xFFFFu);
+    if (s_j >= D.n) {  // never happens for a consistent status word; keep indices valid
+      set_error(p.result, kErrInternal);
+      s_j = 0;
+    }
+  }
+
+  uint32_t E_chunk = E_last;
+  if (fast) {
+    if (lane == 0) {
+      x_k = s_j;
+      if (j == 0) {
+        pre_k = 0;
+        cnt_k = head_cnt + mu;
+        dies_k = (E == dead);
+      } else if (s_j == dead) {
+        dies_k = 1;
+        died_pre = 1;
+        cnt_k = 0;
+      } else {
+        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre_k);
         if (y == dead) {
           dies_k = 1;
           died_pre = 1;
@@ -807,246 +924,248 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
         }
       }
     }
-
-    // 6. start state of the chunk: the end state published by chunk j-1
-    uint32_t s_j = p.init_state;
-    if (j > 0) {
-      unsigned long long w = 0;
-      if (lane == 0) {
-        const long long t0 = clock64();
-        for (;;) {
-          w = ld_acquire(&p.status[j - 1]);
-          if ((w >> 62) != 0) break;
-          if ((uint64_t)(clock64() - t0) > p.wait_budget || read_error(p.result)) {
-            set_error(p.result, kErrTimeout);
-            w = 0;
-            break;
-          }
-        }
-      }
-      w = __shfl_sync(kFull, w, 0);
-      if ((w >> 62) == 0) continue;  // failed: the error word is set
-      s_j = (uint32_t)((w >> 45) & 0xFFFFu);
-      if (s_j >= D.n) {  // never happens for a consistent status word; keep indices valid
-        set_error(p.result, kErrInternal);
-        s_j = 0;
-      }
-    }
-
-    uint32_t E_chunk = E_last;
-    if (fast) {
-      if (lane == 0) {
-        x_k = s_j;
-        if (j == 0) {
-          pre_k = 0;
-          cnt_k = head_cnt + mu;
-          dies_k = (E == dead);
-        } else if (s_j == dead) {
-          dies_k = 1;
-          died_pre = 1;
-          cnt_k = 0;
-        } else {
-          const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre_k);
+  } else {
+    // slow path: walk the rows in order from s_j (lane 0 works, the lanes keep results)
+    uint32_t x = s_j;
+    for (uint32_t k = 0; k < nrows; ++k) {
+      const uint32_t tk = __shfl_sync(kFull, my_t, k);
+      const uint32_t sk = __shfl_sync(kFull, my_sigma, k);
+      const uint32_t Ek = __shfl_sync(kFull, E, k);
+      const uint32_t muk = __shfl_sync(kFull, mu, k);
+      const uint32_t ck = __shfl_sync(kFull, my_conv, k);
+      const uint32_t hk = __shfl_sync(kFull, head_cnt, k);
+      uint32_t cnt = 0, xin = x, pre = 0, dpre = 0;
+      const uint64_t rr = row0 + k;
+      if (p.serial_fallback && !ck && rr != 0 && x != dead) {
+        // unmerged row: the warp runs the resolved start over the whole row
+        x = warp_run_range16(tab, body + rr * p.S, p.S, x, dead, A, &cnt, lane);
+        if (rr == p.R - 1 && p.tail && x != dead) x = run_bytes(tab, body + p.R * p.S, p.tail, x, dead, A, &cnt);
+        if (lane == 0) atomicAdd(&p.result->progress, 1u);
+      } else if (lane == 0) {
+        const uint64_t r = rr;
+        if (x == dead) {
+          dpre = 1;
+        } else if (r == 0) {
+          cnt = hk + muk;
+          x = Ek;
+        } else if (ck) {
+          const uint32_t y = run_range16(tab, body + r * p.S, tk, x, dead, A, &pre);
           if (y == dead) {
-            dies_k = 1;
-            died_pre = 1;
-            cnt_k = pre_k;
-          } else {
-            if (y != my_sigma) set_error(p.result, kErrInternal);
-            cnt_k = pre_k + mu;
-            dies_k = (E == dead);
-          }
-        }
-      }
-    } else {
-      // slow path: walk the rows in order from s_j (lane 0 works, the lanes keep results)
-      uint32_t x = s_j;
-      for (uint32_t k = 0; k < nrows; ++k) {
-        const uint32_t tk = __shfl_sync(kFull, my_t, k);
-        const uint32_t sk = __shfl_sync(kFull, my_sigma, k);
-        const uint32_t Ek = __shfl_sync(kFull, E, k);
-        const uint32_t muk = __shfl_sync(kFull, mu, k);
-        const uint32_t ck = __shfl_sync(kFull, my_conv, k);
-        const uint32_t hk = __shfl_sync(kFull, head_cnt, k);
-        uint32_t cnt = 0, xin = x, pre = 0, dpre = 0;
-        if (lane == 0) {
-          const uint64_t r = row0 + k;
-          if (x == dead) {
+            cnt = pre;
             dpre = 1;
-          } else if (r == 0) {
-            cnt = hk + muk;
-            x = Ek;
-          } else if (ck) {
-            const uint32_t y = run_range16(tab, body + r * p.S, tk, x, dead, A, &pre);
-            if (y == dead) {
-              cnt = pre;
-              dpre = 1;
-              x = dead;
-            } else {
-              if (y != sk) set_error(p.result, kErrInternal);
-              cnt = pre + muk;
-              x = Ek;
-            }
+            x = dead;
           } else {
-            const uint32_t cls = cand_class(r);
-            const uint32_t slot = D.rank[(uint64_t)cls * D.n + x];
-            if (slot == kNoSlot) {
-              set_error(p.result, kErrInternal);
-              x = 0;  // any valid state: the call reports an error
-            } else {
-              cnt = p.slot_cnt[r * p.cand_stride + slot];
-              x = p.slot_end[r * p.cand_stride + slot];
-            }
+            if (y != sk) set_error(p.result, kErrInternal);
+            cnt = pre + muk;
+            x = Ek;
           }
-        }
-        xin = __shfl_sync(kFull, xin, 0);
-        cnt = __shfl_sync(kFull, cnt, 0);
-        pre = __shfl_sync(kFull, pre, 0);
-        dpre = __shfl_sync(kFull, dpre, 0);
-        x = __shfl_sync(kFull, x, 0);
-        if (lane == k) {
-          x_k = xin;
-          cnt_k = cnt;
-          pre_k = pre;
-          died_pre = dpre;
-          dies_k = (x == dead);
-        }
-      }
-      E_chunk = x;
-      if (lane == 0 && !skip) st_release(&p.status[j], pack_status(kFlagMapped, 0, E_chunk, 0));
-    }
-
-    // 7. aggregate: counts up to and including the first row whose run dies
-    const unsigned dmask = __ballot_sync(kFull, active && dies_k);
-    const uint32_t first_dead = dmask ? (uint32_t)(__ffs(dmask) - 1) : 32u;
-    uint64_t c = (active && lane <= first_dead) ? cnt_k : 0;
-    uint64_t csum = c;
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) csum += __shfl_xor_sync(kFull, csum, d);
-    const Pfx agg = {dmask ? 1u : 0u, csum};
-    if (lane == 0 && !skip)
-      st_release(&p.status[j], pack_status(kFlagAggregate, agg.dead, E_chunk, agg.count));
-
-    // 8. decoupled look-back for the exclusive prefix
-    Pfx ex = {0, 0};
-    if (j > 0) {
-      int64_t base = (int64_t)j - 1;
-      bool ok = true;
-      for (;;) {
-        const int64_t idx = base - (int64_t)lane;
-        unsigned long long w = 0;
-        unsigned inc = 0;
-        uint32_t limit = 31;
-        const long long t0 = clock64();
-        for (;;) {
-          w = idx >= 0 ? ld_acquire(&p.status[idx]) : ((unsigned long long)kFlagInclusive << 62);
-          const uint32_t flag = (uint32_t)(w >> 62);
-          inc = __ballot_sync(kFull, flag == kFlagInclusive);
-          const unsigned notready = __ballot_sync(kFull, flag < kFlagAggregate);
-          limit = inc ? (uint32_t)(__ffs(inc) - 1) : 31u;
-          const unsigned need = limit == 31 ? kFull : ((1u << (limit + 1)) - 1u);
-          if (!(notready & need)) break;
-          bool stop = false;
-          if (lane == 0)
-            stop = (uint64_t)(clock64() - t0) > p.wait_budget || read_error(p.result);
-          if (__shfl_sync(kFull, stop, 0)) {
-            ok = false;
-            break;
-          }
-        }
-        if (!ok) break;
-        Pfx v = {0, 0};
-        if (lane <= limit) {
-          v.dead = (uint32_t)((w >> 61) & 1u);
-          v.count = w & kCountMask;
-        }
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          Pfx o;
-          o.dead = __shfl_down_sync(kFull, v.dead, d);
-          o.count = __shfl_down_sync(kFull, v.count, d);
-          if (lane + d < 32) v = pfx_op(o, v);
-        }
-        Pfx win;
-        win.dead = __shfl_sync(kFull, v.dead, 0);
-        win.count = __shfl_sync(kFull, v.count, 0);
-        ex = pfx_op(win, ex);
-        if (inc) break;
-        base -= 32;
-      }
-      if (!ok) {
-        set_error(p.result, kErrTimeout);
-        continue;
-      }
-    }
-    const Pfx inc = pfx_op(ex, agg);
-    if (lane == 0 && !skip)
-      st_release(&p.status[j], pack_status(kFlagInclusive, inc.dead, E_chunk, inc.count));
-
-    // 9. per-row records for the emit pass: offset and the windows holding the matches
-    if (p.segrec != nullptr) {
-      const bool live_row = active && !ex.dead && lane <= first_dead;
-      const uint64_t rc = live_row ? cnt_k : 0;
-      uint64_t incl = rc;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint64_t o = __shfl_up_sync(kFull, incl, d);
-        if (lane >= (uint32_t)d) incl += o;
-      }
-      if (active) {
-        SegRec sr;
-        sr.x = live_row ? x_k : dead;
-        sr.count = (uint32_t)rc;
-        sr.offset = ex.count + incl - rc;
-        sr.flags = 0;
-        sr.t = 0;
-        sr.pre = 0;
-        sr.lvv = kEmpty;
-        sr.ls = 0;
-        if (!my_conv) {
-          // slot-map row: no merged run, replay the whole row from its start
-          sr.fv = 0;
-          sr.fs = x_k;
-          sr.lv = (uint32_t)rowlen;
         } else {
-          if (myrow == 0 && head_cnt > 0) {
-            sr.flags |= kHeadFlag;
-            sr.pre = head_cnt;
-          } else if (pre_k > 0) {
-            sr.flags |= kPreFlag;
-            sr.t = my_t;
-            sr.pre = pre_k;
+          const uint32_t cls = cand_class(r);
+          const uint32_t slot = D.rank[(uint64_t)cls * D.n + x];
+          if (slot == kNoSlot) {
+            set_error(p.result, kErrInternal);
+            x = 0;  // any valid state: the call reports an error
+          } else {
+            cnt = p.slot_cnt[r * p.cand_stride + slot];
+            x = p.slot_end[r * p.cand_stride + slot];
           }
-          // main-run window (empty when the run died inside the prefix)
-          const bool main_live = !died_pre && mu > 0;
-          sr.fv = (main_live && fv != kEmpty) ? fv : 0u;
-          sr.fs = fs;
-          sr.lv = main_live ? lv : 0u;
-          sr.lvv = main_live ? lvv : kEmpty;
-          sr.ls = ls;
-          // every main-run match was recorded by pass 1: the emit pass only copies them
-          if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
         }
-        p.segrec[myrow] = sr;
+      }
+      xin = __shfl_sync(kFull, xin, 0);
+      cnt = __shfl_sync(kFull, cnt, 0);
+      pre = __shfl_sync(kFull, pre, 0);
+      dpre = __shfl_sync(kFull, dpre, 0);
+      x = __shfl_sync(kFull, x, 0);
+      if (lane == k) {
+        x_k = xin;
+        cnt_k = cnt;
+        pre_k = pre;
+        died_pre = dpre;
+        dies_k = (x == dead);
       }
     }
-    if (j == p.n_chunks - 1 && lane == 0) {
-      p.result->final_state = inc.dead ? dead : E_chunk;
-      p.result->count = inc.count;
-    }
+    E_chunk = last_merged ? E_last : x;
+    if (!last_merged && lane == 0 && !skip) st_release(&p.status[j], pack_status(kFlagMapped, 0, E_chunk, 0));
   }
 
-  // drain stages still in flight before the CTA may release its shared memory
+  // 7. aggregate: counts up to and including the first row whose run dies
+  const unsigned dmask = __ballot_sync(kFull, active && dies_k);
+  const uint32_t first_dead = dmask ? (uint32_t)(__ffs(dmask) - 1) : 32u;
+  uint64_t c = (active && lane <= first_dead) ? cnt_k : 0;
+  uint64_t csum = c;
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) csum += __shfl_xor_sync(kFull, csum, d);
+  const Pfx agg = {dmask ? 1u : 0u, csum};
+  if (lane == 0 && !skip)
+    st_release(&p.status[j], pack_status(kFlagAggregate, agg.dead, E_chunk, agg.count));
+
+  // 8. decoupled look-back for the exclusive prefix
+  Pfx ex = {0, 0};
+  if (j > 0) {
+    int64_t base = (int64_t)j - 1;
+    bool ok = true;
+    for (;;) {
+      const int64_t idx = base - (int64_t)lane;
+      unsigned long long w = 0;
+      unsigned inc = 0;
+      uint32_t limit = 31;
+      long long t0 = clock64();
+      uint32_t seen = read_progress(p.result);
+      for (;;) {
+        w = idx >= 0 ? ld_acquire(&p.status[idx]) : ((unsigned long long)kFlagInclusive << 62);
+        const uint32_t flag = (uint32_t)(w >> 62);
+        inc = __ballot_sync(kFull, flag == kFlagInclusive);
+        const unsigned notready = __ballot_sync(kFull, flag < kFlagAggregate);
+        limit = inc ? (uint32_t)(__ffs(inc) - 1) : 31u;
+        const unsigned need = limit == 31 ? kFull : ((1u << (limit + 1)) - 1u);
+        if (!(notready & need)) break;
+        bool stop = false;
+        if (lane == 0) stop = read_error(p.result) || wait_expired(p.result, p.wait_budget, &t0, &seen);
+        if (__shfl_sync(kFull, stop, 0)) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+      Pfx v = {0, 0};
+      if (lane <= limit) {
+        v.dead = (uint32_t)((w >> 61) & 1u);
+        v.count = w & kCountMask;
+      }
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Pfx o;
+        o.dead = __shfl_down_sync(kFull, v.dead, d);
+        o.count = __shfl_down_sync(kFull, v.count, d);
+        if (lane + d < 32) v = pfx_op(o, v);
+      }
+      Pfx win;
+      win.dead = __shfl_sync(kFull, v.dead, 0);
+      win.count = __shfl_sync(kFull, v.count, 0);
+      ex = pfx_op(win, ex);
+      if (inc) break;
+      base -= 32;
+    }
+    if (!ok) {
+      set_error(p.result, kErrTimeout);
+      return;
+    }
+  }
+  const Pfx inc = pfx_op(ex, agg);
+  if (lane == 0 && !skip)
+    st_release(&p.status[j], pack_status(kFlagInclusive, inc.dead, E_chunk, inc.count));
+
+  // 9. per-row records for the emit pass: offset and the windows holding the matches
+  if (p.segrec != nullptr) {
+    const bool live_row = active && !ex.dead && lane <= first_dead;
+    const uint64_t rc = live_row ? cnt_k : 0;
+    uint64_t incl = rc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t o = __shfl_up_sync(kFull, incl, d);
+      if (lane >= (uint32_t)d) incl += o;
+    }
+    if (active) {
+      SegRec sr;
+      sr.x = live_row ? x_k : dead;
+      sr.count = (uint32_t)rc;
+      sr.offset = ex.count + incl - rc;
+      sr.flags = 0;
+      sr.t = 0;
+      sr.pre = 0;
+      sr.lvv = kEmpty;
+      sr.ls = 0;
+      if (!my_conv) {
+        // slot-map row: no merged run, replay the whole row from its start
+        sr.fv = 0;
+        sr.fs = x_k;
+        sr.lv = (uint32_t)rowlen;
+      } else {
+        if (myrow == 0 && head_cnt > 0) {
+          sr.flags |= kHeadFlag;
+          sr.pre = head_cnt;
+        } else if (pre_k > 0) {
+          sr.flags |= kPreFlag;
+          sr.t = my_t;
+          sr.pre = pre_k;
+        }
+        // main-run window (empty when the run died inside the prefix)
+        const bool main_live = !died_pre && mu > 0;
+        sr.fv = (main_live && fv != kEmpty) ? fv : 0u;
+        sr.fs = fs;
+        sr.lv = main_live ? lv : 0u;
+        sr.lvv = main_live ? lvv : kEmpty;
+        sr.ls = ls;
+        // every main-run match was recorded by pass 1: the emit pass only copies them
+        if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
+      }
+      p.segrec[myrow] = sr;
+    }
+  }
+  if (j == p.n_chunks - 1 && lane == 0) {
+    p.result->final_state = inc.dead ? dead : E_chunk;
+    p.result->count = inc.count;
+  }
+}
+
+// Wait (bounded) for stages still in flight before the CTA may release its shared memory.
+__device__ __forceinline__ void drain_stages(const WarpCtx& wc, uint64_t budget) {
   for (uint32_t b = 0; b < kStages; ++b) {
-    if (pending & (1u << b)) {
-      const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
+    if (wc.pending & (1u << b)) {
+      const uint32_t bar = smem_u32(wc.sm + wc.bar0 + 8 * b);
       const long long t0 = clock64();
-      while (!mbar_try_wait(bar, (phase_bits >> b) & 1u)) {
-        if ((uint64_t)(clock64() - t0) > p.wait_budget) break;
+      while (!mbar_try_wait(bar, (wc.phase_bits >> b) & 1u)) {
+        if ((uint64_t)(clock64() - t0) > budget) break;
       }
     }
   }
 }
+
+// ---------------------------------------------------------------------------------------
+// Pass 1: speculation, main run, look-back.  P = candidate registers per lane when one row
+// is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
+// ---------------------------------------------------------------------------------------
+template <int LAYOUT, int ESIZE, int P>
+__global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
+    k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  load_tables<LAYOUT, ESIZE>(sm, p.dfa);
+  const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
+  WarpCtx wc;
+  wc.sm = sm;
+  wc.lane = lane;
+  wc.stage0 = region + warp * (kStages * kStageBytes);
+  wc.bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
+  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * p.spec_bytes;
+  wc.hand = reinterpret_cast<uint16_t*>(sm + spec0);
+  wc.cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
+  // 2 x bitmap_words words of candidate bitmaps, then a list of up to 256 states
+  wc.bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
+  wc.phase_bits = 0;
+  wc.pending = 0;
+  if (lane == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + wc.bar0 + 8 * s), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  Tab<LAYOUT, ESIZE> tab;
+  tab.sm = sm;
+  tab.gtable = p.dfa.table;
+  tab.rowbytes = p.dfa.rowbytes;
+  tab.smem_tier = 1;
+  for (;;) {
+    uint32_t ticket = 0;
+    if (lane == 0) ticket = read_error(p.result) ? 0xFFFFFFFFu : atomicAdd(p.ticket, 1u);
+    ticket = __shfl_sync(kFull, ticket, 0);
+    if ((uint64_t)ticket >= p.n_chunks) break;
+    scan_chunk<LAYOUT, ESIZE, P>(wc, tab, p, &tmap, ticket);
+  }
+  drain_stages(wc, p.wait_budget);
+}
+
 
 // ---------------------------------------------------------------------------------------
 // Emit pass: one thread per row with matches.  It first replays the first and the last
@@ -1092,6 +1211,52 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
   }
 }
 
+// The positions of row r of one text (see k_emit).
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void emit_row(const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p, uint64_t r) {
+  const uint32_t A = p.dfa.first_accept;
+  const SegRec sr = p.segrec[r];
+  if (sr.count == 0 || sr.offset >= p.capacity) return;
+  const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
+  uint64_t o = sr.offset;
+  if (sr.flags & kHeadFlag) {
+    // row 0: the unaligned head bytes before the first full row
+    uint32_t x = sr.x;
+    for (uint64_t i = 0; i < p.h && o < end; ++i) {
+      x = tab.next(x, tab.col(ldg8(p.text + i)));
+      if (x >= A) p.positions[o++] = i;
+    }
+  } else if (sr.flags & kPreFlag) {
+    // matches inside the merged prefix [0, t), replayed from the row's true start
+    uint32_t x = sr.x;
+    emit_range(tab, p, r, 0u, sr.t, x, o, end);
+  }
+  if (o >= end || sr.lv == 0) return;
+  if (sr.flags & kSlotsFlag) {
+    // pass 1 recorded every main-run match of this row
+    const uint64_t gbase = p.h + r * p.S;
+    const uint32_t* sl = p.slots + r * kRowSlots;
+    for (uint32_t i = 0; o < end; ++i) p.positions[o++] = gbase + sl[i];
+    return;
+  }
+  atomicAdd(&p.result->emit_replays, 1u);
+  atomicMax(&p.result->emit_max_window, sr.lv - sr.fv);
+  const uint64_t o_main = o;
+  uint32_t x = sr.fs;
+  if (sr.lvv != kEmpty && sr.lvv > sr.fv) {
+    // fast replay: the first matching vector, then the last one
+    const uint32_t first_end = sr.fv + 16 <= sr.lvv ? sr.fv + 16 : sr.lvv;
+    emit_range(tab, p, r, sr.fv, first_end, x, o, end);
+    uint32_t y = sr.ls;
+    emit_range(tab, p, r, sr.lvv, sr.lv, y, o, end);
+    if (o == end) return;
+    // matches lie between the two vectors: replay the whole window
+    o = o_main;
+    x = sr.fs;
+  }
+  emit_range(tab, p, r, sr.fv, sr.lv, x, o, end);
+}
+
 template <int LAYOUT, int ESIZE>
 __global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -1103,50 +1268,10 @@ __global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
   tab.sm = sm;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
-  const uint32_t A = D.first_accept;
+  tab.smem_tier = 1;
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
-       r += (uint64_t)gridDim.x * blockDim.x) {
-    const SegRec sr = p.segrec[r];
-    if (sr.count == 0 || sr.offset >= p.capacity) continue;
-    const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
-    uint64_t o = sr.offset;
-    if (sr.flags & kHeadFlag) {
-      // row 0: the unaligned head bytes before the first full row
-      uint32_t x = sr.x;
-      for (uint64_t i = 0; i < p.h && o < end; ++i) {
-        x = tab.next(x, tab.col(ldg8(p.text + i)));
-        if (x >= A) p.positions[o++] = i;
-      }
-    } else if (sr.flags & kPreFlag) {
-      // matches inside the merged prefix [0, t), replayed from the row's true start
-      uint32_t x = sr.x;
-      emit_range(tab, p, r, 0u, sr.t, x, o, end);
-    }
-    if (o >= end || sr.lv == 0) continue;
-    if (sr.flags & kSlotsFlag) {
-      // pass 1 recorded every main-run match of this row
-      const uint64_t gbase = p.h + r * p.S;
-      const uint32_t* sl = p.slots + r * kRowSlots;
-      for (uint32_t i = 0; o < end; ++i) p.positions[o++] = gbase + sl[i];
-      continue;
-    }
-    atomicAdd(&p.result->emit_replays, 1u);
-    atomicMax(&p.result->emit_max_window, sr.lv - sr.fv);
-    const uint64_t o_main = o;
-    uint32_t x = sr.fs;
-    if (sr.lvv != kEmpty && sr.lvv > sr.fv) {
-      // fast replay: the first matching vector, then the last one
-      const uint32_t first_end = sr.fv + 16 <= sr.lvv ? sr.fv + 16 : sr.lvv;
-      emit_range(tab, p, r, sr.fv, first_end, x, o, end);
-      uint32_t y = sr.ls;
-      emit_range(tab, p, r, sr.lvv, sr.lv, y, o, end);
-      if (o == end) continue;
-      // matches lie between the two vectors: replay the whole window
-      o = o_main;
-      x = sr.fs;
-    }
-    emit_range(tab, p, r, sr.fv, sr.lv, x, o, end);
-  }
+       r += (uint64_t)gridDim.x * blockDim.x)
+    emit_row<LAYOUT, ESIZE>(tab, p, r);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1164,6 +1289,7 @@ __global__ void k_tiny(const ScanParams p) {
   tab.sm = sm;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
+  tab.smem_tier = 1;
   uint32_t x = p.init_state;
   uint64_t cnt = 0;
   for (uint64_t i = 0; i < p.n; ++i) {
@@ -1177,6 +1303,128 @@ __global__ void k_tiny(const ScanParams p) {
   p.result->final_state = x;
   p.result->count = cnt;
 }
+
+#ifdef PAREM_BATCH_KERNELS  // compiled in parem_k_batch.cu only
+// ---------------------------------------------------------------------------------------
+// Batch: many (text, DFA) items in one persistent launch.  Each CTA serves one slot (DFA) at
+// a time: it stages that DFA's tables once, its warps take the slot's chunk tickets (the
+// chunks of all the slot's items in order), and when the slot runs dry the CTA moves to
+// another slot that still has chunks.  Within a slot the chunk protocol is the one of
+// k_spec_scan, per item.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  __shared__ uint32_t s_next;
+  uint8_t* const sm = smem_raw;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t region = stage_region_off(smem_raw, bp.max_table_smem);
+  WarpCtx wc;
+  wc.sm = sm;
+  wc.lane = lane;
+  wc.stage0 = region + warp * (kStages * kStageBytes);
+  wc.bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
+  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * bp.spec_bytes;
+  wc.hand = reinterpret_cast<uint16_t*>(sm + spec0);
+  wc.cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
+  wc.bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
+  wc.phase_bits = 0;
+  wc.pending = 0;
+  if (lane == 0) {
+    for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + wc.bar0 + 8 * s), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  uint32_t slot = bp.cta_slot[blockIdx.x];
+  while (slot < bp.n_slots) {
+    const BatchSlot& S = bp.slots[slot];
+    load_tables_dyn(sm, S.dfa, S.smem_tier);
+    __syncthreads();
+    Tab<kBatchDyn, 2> tab;
+    tab.sm = sm;
+    tab.gtable = S.dfa.table;
+    tab.rowbytes = S.dfa.rowbytes;
+    tab.smem_tier = S.smem_tier;
+    for (;;) {
+      uint32_t ticket = 0;
+      if (lane == 0) ticket = atomicAdd(S.ticket, 1u);
+      ticket = __shfl_sync(kFull, ticket, 0);
+      if ((uint64_t)ticket >= S.n_chunks) break;
+      // the item that owns this chunk: the last one whose first ticket is <= ticket
+      uint32_t lo = S.item_begin, hi = S.item_end - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (bp.items[mid].chunk_base <= ticket) lo = mid; else hi = mid - 1;
+      }
+      const BatchItem& it = bp.items[lo];
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it.tmap) : "memory");
+      scan_chunk<kBatchDyn, 2, 8>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
+    }
+    __syncthreads();  // every warp is done with this slot's tables
+    if (threadIdx.x == 0) {
+      uint32_t nx = 0xFFFFFFFFu;
+      for (uint32_t k = 1; k <= bp.n_slots; ++k) {
+        const uint32_t c = (slot + k) % bp.n_slots;
+        if ((uint64_t)*reinterpret_cast<volatile uint32_t*>(bp.slots[c].ticket) < bp.slots[c].n_chunks) {
+          nx = c;
+          break;
+        }
+      }
+      s_next = nx;
+    }
+    __syncthreads();
+    slot = s_next;
+  }
+  drain_stages(wc, bp.wait_budget);
+}
+
+// Batch emit: each CTA handles 256 rows of one slot's items.
+__global__ void __launch_bounds__(256) k_batch_emit(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const uint32_t slot = bp.emit_slot[blockIdx.x];
+  const BatchSlot& S = bp.slots[slot];
+  load_tables_dyn(sm, S.dfa, S.smem_tier);
+  __syncthreads();
+  Tab<kBatchDyn, 2> tab;
+  tab.sm = sm;
+  tab.gtable = S.dfa.table;
+  tab.rowbytes = S.dfa.rowbytes;
+  tab.smem_tier = S.smem_tier;
+  const uint64_t rr = bp.emit_row0[blockIdx.x] + threadIdx.x;
+  if (rr >= S.n_rows) return;
+  uint32_t lo = S.item_begin, hi = S.item_end - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) / 2;
+    if (bp.items[mid].row_base <= rr) lo = mid; else hi = mid - 1;
+  }
+  const BatchItem& it = bp.items[lo];
+  if (it.p.segrec == nullptr || it.p.R == 0) return;
+  emit_row<kBatchDyn, 2>(tab, it.p, rr - it.row_base);
+}
+
+// Batch items too short for one row: one thread per item.
+__global__ void k_batch_tiny(const __grid_constant__ BatchParams bp, const uint32_t* tiny_items, uint32_t n_tiny) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiny) return;
+  const BatchItem& it = bp.items[tiny_items[t]];
+  const ScanParams& p = it.p;
+  const DeviceDfa& D = p.dfa;
+  uint32_t x = p.init_state;
+  uint64_t cnt = 0;
+  for (uint64_t i = 0; i < p.n; ++i) {
+    if (x == D.dead) break;
+    const uint32_t c = *reinterpret_cast<const uint16_t*>(D.colmap + 2 * ldg8(p.text + i));
+    x = __ldg(reinterpret_cast<const uint16_t*>(D.table + x * D.rowbytes + c));
+    if (x >= D.first_accept) {
+      if (p.positions && cnt < p.capacity) p.positions[cnt] = i;
+      ++cnt;
+    }
+  }
+  p.result->final_state = x;
+  p.result->count = cnt;
+}
+
+#endif  // PAREM_BATCH_KERNELS
 
 // Launch wrappers, instantiated in the per-layout translation units.
 template <int LAYOUT, int ESIZE, int P>

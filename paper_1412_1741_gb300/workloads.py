@@ -331,3 +331,123 @@ def gattaca_workload(n: int = 1 << 20):
 
 def parallel_workload(n: int, seed: int = 11):
     return parallel_dfa(), uniform_text(n, 5, seed)
+
+
+# ----------------------------------------------------------------------------------------
+# Batched workload: many texts of uneven length, each paired with one of several DFAs
+# ----------------------------------------------------------------------------------------
+def keyword_union_dfa(target_states: int, alphabet: int, seed: int):
+    """Aho-Corasick DFA of random keywords over `alphabet` symbols, adding keywords (lengths
+    4-16) until the trie has at least `target_states` states.  For the 27-symbol alphabet the
+    keywords use the letters only (symbol 26 is the space)."""
+    rng = np.random.default_rng(seed)
+    letters = 26 if alphabet == 27 else alphabet
+    kws, nodes = [], {()}
+    while len(nodes) < target_states:
+        kw = tuple(int(x) for x in rng.integers(0, letters, size=int(rng.integers(4, 17))))
+        kws.append(kw)
+        for i in range(1, len(kw) + 1):
+            nodes.add(kw[:i])
+    table, accept = aho_corasick_dfa(kws, alphabet)
+    return table, accept, kws
+
+
+def batch_dfas(n_dfas: int = 32, seed: int = 6, max_states: int = 4096):
+    """DFAs of the batched workload: states log-uniform in [4, max_states], alphabet uniform
+    over {4, 27, 256}; even ids are keyword unions, odd ids random complete DFAs (10%
+    accepting).  Byte maps: 27 symbols use letters_byte_map, 4 and 256 the identity."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n_dfas):
+        states = int(round(np.exp(rng.uniform(np.log(4), np.log(max_states)))))
+        alphabet = int(rng.choice([4, 27, 256]))
+        if d % 2 == 0:
+            table, accept, kws = keyword_union_dfa(states, alphabet, seed * 1000 + d)
+            meta = {"family": "keywords", "alphabet": alphabet, "keywords": len(kws)}
+        else:
+            table, accept = random_dfa(states, alphabet, max(1, int(round(0.1 * states))), seed * 1000 + d)
+            meta = {"family": "random", "alphabet": alphabet}
+        b2s = letters_byte_map() if alphabet == 27 else None
+        out.append(DfaSpec(table, 0, accept, b2s, f"batch{d}", meta))
+    return out
+
+
+def batch_lengths(n_texts: int = 4096, lo: int = 1 << 10, hi: int = 16 << 20, seed: int = 6):
+    """Text lengths log-uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed + 100)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_texts)).astype(np.int64)
+
+
+def batch_texts_device(dfas, lengths, device, seed: int = 6, pool_bytes: int = 64 << 20):
+    """Texts of the batched workload in one device arena (each text its own bytes): text i
+    goes with DFA i mod len(dfas).  Keyword DFAs read Zipf words mapped into their alphabet
+    (letters and space as is for 27 and 256 symbols; (letter - 'a') mod 4 and space -> 0 for
+    4 symbols); random DFAs read uniform symbols.  Texts are copied from seeded pools at
+    seeded offsets.  Returns (arena, offsets)."""
+    import torch
+
+    pool_bytes = max(pool_bytes, int(lengths.max()) + 1)
+    zipf = zipf_words_text_device(pool_bytes, device, seed=seed)
+    z4 = torch.where(zipf == 32, torch.zeros_like(zipf), (zipf - 97) % 4)
+    pools = {("keywords", 27): zipf, ("keywords", 256): zipf, ("keywords", 4): z4,
+             ("random", 4): uniform_text_device(pool_bytes, 4, device, seed + 1),
+             ("random", 27): uniform_text_device(pool_bytes, 27, device, seed + 2),
+             ("random", 256): uniform_text_device(pool_bytes, 256, device, seed + 3)}
+    offsets = np.zeros(len(lengths) + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lengths)
+    arena = torch.empty(int(offsets[-1]), dtype=torch.uint8, device=device)
+    rng = np.random.default_rng(seed + 200)
+    for i, L in enumerate(lengths):
+        spec = dfas[i % len(dfas)]
+        pool = pools[(spec.meta["family"], spec.meta["alphabet"])]
+        start = int(rng.integers(0, pool_bytes - int(L)))
+        arena[int(offsets[i]):int(offsets[i + 1])] = pool[start:start + int(L)]
+    return arena, offsets
+
+
+# ---------------------------------------------------------------------------------------
+# serving workload: 128 DFAs, Poisson arrivals of requests that are slices of device pools
+# ---------------------------------------------------------------------------------------
+def serve_dfas(n_dfas: int = 128, seed: int = 7, max_states: int = 8192):
+    """DFAs of the serving workload: the batch families with states log-uniform in
+    [4, max_states]."""
+    return batch_dfas(n_dfas, seed=seed, max_states=max_states)
+
+
+def serve_trace(n_dfas: int, rate_per_s: float, duration_s: float, lo: int = 256, hi: int = 64 << 20,
+                seed: int = 7):
+    """Open-loop request trace: exponential inter-arrival gaps at rate_per_s for duration_s,
+    DFA uniform over n_dfas, lengths log-uniform in [lo, hi].  Returns (arrival_ns, dfa, length)."""
+    rng = np.random.default_rng(seed)
+    n = int(rate_per_s * duration_s * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+    n = int(np.searchsorted(t, duration_s))
+    arrival = (t[:n] * 1e9).astype(np.int64)
+    dfa = rng.integers(0, n_dfas, size=n).astype(np.uint32)
+    length = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n)).astype(np.int64)
+    return arrival, dfa, length
+
+
+def serve_pools_device(device, pool_bytes: int = 1536 << 20, seed: int = 7):
+    """Device text pools of the serving workload, one per (family, alphabet), filled as the
+    batched workload's texts: 6 x pool_bytes (9 GiB at the default)."""
+    import torch
+
+    zipf = zipf_words_text_device(pool_bytes, device, seed=seed)
+    z4 = torch.where(zipf == 32, torch.zeros_like(zipf), (zipf - 97) % 4)
+    return {("keywords", 27): zipf, ("keywords", 256): zipf.clone(), ("keywords", 4): z4,
+            ("random", 4): uniform_text_device(pool_bytes, 4, device, seed + 1),
+            ("random", 27): uniform_text_device(pool_bytes, 27, device, seed + 2),
+            ("random", 256): uniform_text_device(pool_bytes, 256, device, seed + 3)}
+
+
+def serve_slices(specs, pools, dfa, length, seed: int = 7):
+    """Device address of each request's text: a seeded slice of its DFA's pool."""
+    rng = np.random.default_rng(seed + 300)
+    addr = np.zeros(len(dfa), dtype=np.uint64)
+    keys = [(s.meta["family"], s.meta["alphabet"]) for s in specs]
+    for i, (d, L) in enumerate(zip(dfa, length)):
+        pool = pools[keys[int(d)]]
+        start = int(rng.integers(0, pool.numel() - int(L)))
+        addr[i] = pool.data_ptr() + start
+    return addr

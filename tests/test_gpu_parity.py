@@ -200,7 +200,7 @@ def test_host_buffers(torch):
     assert np.array_equal(pos[:got.n_written], want.positions)
 
 
-@pytest.mark.parametrize("n_states,n_sym,layout", [(300, 140, 3), (300, 200, 4), (150, 4, 0), (700, 30, 1)])
+@pytest.mark.parametrize("n_states,n_sym,layout", [(400, 140, 3), (450, 200, 4), (150, 4, 0), (700, 30, 1)])
 def test_table_layouts_and_register_counts(torch, n_states, n_sym, layout):
     t, acc = wl.random_dfa(n_states, n_sym, max(1, n_states // 10), seed=n_states + n_sym)
     spec = wl.DfaSpec(t, 0, acc, None, f"rand{n_states}x{n_sym}")

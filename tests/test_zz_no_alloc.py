@@ -64,13 +64,19 @@ def test_noalloc_matches_parem_match_on_two_calls_in_a_row(torch):
 
 
 def test_noalloc_rejects_requests_beyond_the_fixed_area(torch):
-    # 5000 states over 4 symbols: ~3160 candidates per class, so the slot maps of a 64 MiB
-    # text need far more than the 16 MiB area
-    t, acc = wl.random_dfa(5000, 4, 500, seed=5)
-    dfa = pm.parem_load_dfa(t, None, 0, acc)
-    text = torch.zeros(64 << 20, dtype=torch.uint8, device="cuda")
+    # with positions requested, every row of the scan keeps a record and recorded positions
+    # (112 bytes): a 256 MiB text has ~300k rows of under 1 KiB for the 8-state GATTACA DFA,
+    # far more than the 16 MiB area holds
+    spec = wl.gattaca_dfa()
+    dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    text = torch.zeros(256 << 20, dtype=torch.uint8, device="cuda")
+    pos = torch.full((16,), -1, dtype=torch.int64, device="cuda")
     with pytest.raises(pm.ParemError) as e:
-        pm.parem_match_noalloc(dfa, text)
+        pm.parem_match_noalloc(dfa, text, pos)
     assert e.value.status == pm.PAREM_ERR_TOO_LARGE
     assert "fixed area" in pm.parem_strerror(pm.PAREM_ERR_TOO_LARGE)
+    assert bool((pos == -1).all())  # nothing written
+    # the same text without positions fits
+    got = pm.parem_match_noalloc(dfa, text)
+    assert (got.final_state, got.match_count) == (0, 0)
     dfa.free()
