@@ -92,10 +92,10 @@ typedef struct {
 
 /* Options of parem_match_ex; zero-initialise, then set what you need. */
 typedef struct {
-  uint32_t start_state;     /* PAREM_NONE (or 0xFFFFFFFF): the DFA's start q0.  Otherwise the
-                               state carried in from the end of a previous piece of a stream
-                               (original numbering), so a long text can be matched piecewise:
-                               positions are then relative to this piece. */
+  uint32_t start_state;     /* with use_start_state = 1: the state carried in from the end of
+                               a previous piece of a stream (original numbering), so a long
+                               text can be matched piecewise; positions are then relative to
+                               this piece.  Ignored otherwise (the run starts at q0). */
   uint32_t enumerate_all;   /* 1: speculate every state as a chunk's candidate (the general
                                enumeration approach the paper compares against, Section IV-A)
                                instead of the candidate set of Algorithm 1. */
@@ -106,12 +106,12 @@ typedef struct {
                                converging; 0 = planner's choice */
   uint64_t wait_budget_cycles; /* bound of every device-side wait, in SM clock cycles;
                                   0 = about 2 seconds */
-  int64_t debug_skip_publish_chunk; /* test hook, -1 = off: the chunk with this index never
-                                       publishes its state, so its successor's bounded wait
-                                       runs out and the call returns PAREM_ERR_TIMEOUT */
+  int64_t debug_skip_publish_chunk; /* test hook, 0 = off: a positive k makes chunk k never
+                                       publish its state, so its successor's bounded wait runs
+                                       out and the call returns PAREM_ERR_TIMEOUT */
   uint32_t record_kernel_times; /* 1: record CUDA events around each kernel of the call on the
                                    call's stream; read them with parem_last_stats */
-  uint32_t reserved;
+  uint32_t use_start_state; /* 1: start from start_state instead of q0 */
 } parem_match_opts;
 
 /* What the last scan on a (device, stream) did: its plan and, when record_kernel_times was
@@ -130,9 +130,14 @@ typedef struct {
   uint32_t emit_replays;    /* rows whose positions the emit pass replayed (not recorded in pass 1) */
   uint32_t emit_max_window; /* longest window (bytes) the emit pass replayed */
   uint32_t nonconv_rows;    /* rows whose candidates did not merge within the speculation cap
-                               (they fall back to per-candidate slot maps) */
+                               (resolved through slot maps or a run from the resolved start) */
   uint32_t conv_max;        /* longest speculative prefix a row needed before its candidates
                                merged (bytes); later plans for the DFA use longer rows */
+  /* SM cycles of the warps owning chunks, summed over chunks: speculation (including slot
+     maps), main run, resolution (waits on predecessors, look-back, row records) */
+  uint64_t cycles_spec, cycles_main, cycles_resolve;
+  uint64_t cycles_bitmap, cycles_lane;  /* parts of cycles_spec: the bitmap phase of large
+                                           candidate sets, the lane phase of the survivors */
 } parem_stats;
 
 /*
@@ -278,6 +283,10 @@ int parem_batch_results(const parem_batch* batch, parem_result* out);
 
 /* Segment size chosen for item i (planner or autotuner).  Errors: INVALID_ARG. */
 int parem_batch_item_segment(const parem_batch* batch, uint32_t i, uint64_t* segment_bytes);
+
+/* Counters of the last run summed over the batch's items (the plan fields are 0; unmerged
+ * rows, longest merge, kernels and the cycle counters are filled).  Errors: INVALID_ARG. */
+int parem_batch_stats(const parem_batch* batch, parem_stats* out);
 
 /* Free a batch (NULL is ignored). */
 void parem_batch_free(parem_batch* batch);

@@ -46,7 +46,7 @@ EXPORTED_SYMBOLS = [
     "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
     "parem_last_stats", "parem_match_noalloc", "parem_batch_create", "parem_batch_run", "parem_batch_results",
-    "parem_batch_item_segment", "parem_batch_free", "parem_server_create", "parem_server_submit",
+    "parem_batch_item_segment", "parem_batch_stats", "parem_batch_free", "parem_server_create", "parem_server_submit",
     "parem_server_poll", "parem_server_drain", "parem_server_replay", "parem_server_get_stats",
     "parem_server_free", "parem_clock_ns",
 ]
@@ -78,12 +78,14 @@ class MatchOpts(ctypes.Structure):
                 ("segment_bytes", ctypes.c_uint64), ("warps_per_block", ctypes.c_uint32),
                 ("spec_cap_bytes", ctypes.c_uint32), ("wait_budget_cycles", ctypes.c_uint64),
                 ("debug_skip_publish_chunk", ctypes.c_int64), ("record_kernel_times", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("use_start_state", ctypes.c_uint32)]
 
     def __init__(self, start_state=PAREM_NONE, enumerate_all=0, segment_bytes=0, warps_per_block=0,
-                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=-1, record_kernel_times=0):
-        super().__init__(start_state, enumerate_all, segment_bytes, warps_per_block, spec_cap_bytes,
-                         wait_budget_cycles, debug_skip_publish_chunk, record_kernel_times, 0)
+                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=0, record_kernel_times=0):
+        # start_state PAREM_NONE: start at the DFA's q0
+        use = 0 if start_state == PAREM_NONE else 1
+        super().__init__(0 if not use else start_state, enumerate_all, segment_bytes, warps_per_block,
+                         spec_cap_bytes, wait_budget_cycles, debug_skip_publish_chunk, record_kernel_times, use)
 
 
 class Stats(ctypes.Structure):
@@ -92,7 +94,10 @@ class Stats(ctypes.Structure):
                 ("warps_per_block", ctypes.c_uint32), ("candidate_regs", ctypes.c_uint32),
                 ("spec_cap_bytes", ctypes.c_uint32), ("kernels", ctypes.c_uint32),
                 ("emit_replays", ctypes.c_uint32), ("emit_max_window", ctypes.c_uint32),
-                ("nonconv_rows", ctypes.c_uint32), ("conv_max", ctypes.c_uint32)]
+                ("nonconv_rows", ctypes.c_uint32), ("conv_max", ctypes.c_uint32),
+                ("cycles_spec", ctypes.c_uint64), ("cycles_main", ctypes.c_uint64),
+                ("cycles_resolve", ctypes.c_uint64), ("cycles_bitmap", ctypes.c_uint64),
+                ("cycles_lane", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -365,6 +370,8 @@ def _bind_batch(lib):
     lib.parem_batch_results.restype = ctypes.c_int
     lib.parem_batch_item_segment.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
     lib.parem_batch_item_segment.restype = ctypes.c_int
+    lib.parem_batch_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.parem_batch_stats.restype = ctypes.c_int
     lib.parem_batch_free.argtypes = [vp]
     lib.parem_batch_free.restype = None
     lib._batch_bound = True
@@ -401,6 +408,13 @@ class Batch:
             lib.parem_batch_item_segment(self._h, i, ctypes.byref(v))
             out.append(v.value)
         return out
+
+    def stats(self) -> dict:
+        st = Stats()
+        rc = load_library().parem_batch_stats(self._h, ctypes.byref(st))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_batch_stats")
+        return st.as_dict()
 
     def free(self):
         if self._h is not None:

@@ -42,6 +42,9 @@ struct Scratch {
   size_t text_bytes = 0;
   void* dev_pos = nullptr;
   size_t pos_bytes = 0;
+  cudaStream_t copy_st[2] = {nullptr, nullptr};  // host-text pieces are copied on these
+  std::vector<cudaEvent_t> piece_ev;              // one per piece: its copy has landed
+  cudaEvent_t host_ev = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before pass 1, after pass 1, after emit
   bool timed = false, emitted = false, have_stats = false;
   parem_stats stats{};
@@ -317,8 +320,17 @@ extern "C" int parem_release_scratch(void* stream) {
 // ---------------------------------------------------------------------------------------
 namespace parem {
 
-// Row length in units of the synchronisation length (measured: see the planner notes).
-constexpr uint64_t kRowsPerSync = 8;
+// Candidate sets of DFAs with at least 256 states that take longer than this to shrink to
+// one state (estimated, symbols) merge through the state bitmap every 16 steps: merging
+// with match_any only finds equal states within one register, so a long shrinking phase
+// would keep every register live.
+constexpr uint32_t kBitmapSync = 16;
+
+// Row length in units of the estimated synchronisation length, and in units of the longest
+// merge seen so far (measured on random DFAs with 126 to 2,000 states and 1 GiB of text:
+// throughput rises up to 16-32 x the estimate, where the speculation is a small part of a row).
+constexpr uint64_t kRowsPerSync = 16;
+constexpr uint64_t kRowsPerMerge = 2;
 
 bool serial_rows(const parem_dfa* dfa, uint32_t m) { return m > kLanes && dfa->host.sync_len != kNoSync; }
 
@@ -336,7 +348,7 @@ uint64_t min_row_bytes(const parem_dfa* dfa, uint32_t P) {
   // rows several times longer than the candidates need to merge: the estimate from random
   // input (prepare time) or the longest merge seen on real input, whichever is larger
   const uint64_t est = H.sync_len == kNoSync ? 0 : H.sync_len;
-  smin = std::max<uint64_t>(smin, kRowsPerSync * std::max<uint64_t>(est, dfa->conv_hint.load()));
+  smin = std::max<uint64_t>(smin, std::max<uint64_t>(kRowsPerSync * est, kRowsPerMerge * dfa->conv_hint.load()));
   smin = std::min<uint64_t>(round_up(smin, kBox), 64u << 20);
   return std::min(smin, max_row_bytes(dfa, H.max_cand));
 }
@@ -375,7 +387,8 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   const uint32_t fixed = kTableOff + table_smem + 1024;
   // candidate sets larger than the registers run through a per-warp bitmap of the states
   pl->bitmap_words = 0;
-  if (pl->P > 1 && m_need > 32u * pl->P && P.n <= 16384) pl->bitmap_words = (P.n + 31) / 32;
+  if (pl->P > 1 && P.n <= 16384 && (m_need > 32u * pl->P || (P.sync_len > kBitmapSync && P.n >= 256)))
+    pl->bitmap_words = (P.n + 31) / 32;
   pl->spec_bytes = kSpecBytes + (pl->bitmap_words ? (uint32_t)round_up(8ull * pl->bitmap_words, 16) + 512u : 0u);
   const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + pl->spec_bytes;
   int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
@@ -431,10 +444,11 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
 }  // namespace parem
 
 static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
-                    uint64_t capacity, const parem_match_opts* o, cudaStream_t stream, parem_result* out) {
+                    uint64_t capacity, const parem_match_opts* o, cudaStream_t stream, parem_result* out,
+                    uint64_t pos_base = 0) {
   const Prepared& P = dfa->host;
   uint32_t init = P.start;
-  if (o && o->start_state != PAREM_NONE) {
+  if (o && o->use_start_state) {
     if (o->start_state >= P.n_in) return PAREM_ERR_INVALID_ARG;
     init = P.compact_of[o->start_state];
   }
@@ -484,8 +498,9 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.spec_cap = pl.spec_cap;
   p.cand_stride = pl.cand_stride;
   p.serial_fallback = pl.serial;
+  p.pos_base = pos_base;
   p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
-  p.skip_publish = o ? o->debug_skip_publish_chunk : -1;
+  p.skip_publish = (o && o->debug_skip_publish_chunk > 0) ? o->debug_skip_publish_chunk : -1;
   if (!o) p.skip_publish = -1;
   p.ticket = reinterpret_cast<uint32_t*>(sb);
   p.result = reinterpret_cast<DevResult*>(sb + 256);
@@ -541,6 +556,11 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   sc->stats.emit_max_window = r.emit_max_window;
   sc->stats.nonconv_rows = r.nonconv_rows;
   sc->stats.conv_max = r.conv_max;
+  sc->stats.cycles_spec = r.cyc_spec;
+  sc->stats.cycles_main = r.cyc_main;
+  sc->stats.cycles_resolve = r.cyc_resolve;
+  sc->stats.cycles_bitmap = r.cyc_bitmap;
+  sc->stats.cycles_lane = r.cyc_lane;
   if (pl.R) learn_convergence(dfa, pl.spec_cap, r.nonconv_rows, r.conv_max);
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
@@ -583,13 +603,69 @@ extern "C" int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint6
     rc = ensure(&sc->dev_pos, &sc->pos_bytes, capacity * 8);
     if (rc != PAREM_OK) return rc;
   }
-  if (len) PAREM_CUDA_TRY(cudaMemcpyAsync(sc->dev_text, text, len, cudaMemcpyHostToDevice, st));
-  rc = run_scan(dfa, static_cast<const uint8_t*>(sc->dev_text), len,
-                want ? static_cast<uint64_t*>(sc->dev_pos) : nullptr, want ? capacity : 0, nullptr, st, out);
-  if (rc != PAREM_OK && rc != PAREM_ERR_CAPACITY) return rc;
+  std::memset(out, 0, sizeof(*out));
+  // Pieces of the text are copied on two copy streams, all enqueued at once; each piece is
+  // scanned as soon as it has landed, from the state the previous piece ended in (the
+  // carry-in start of the scan), while the later pieces are still being copied.
+  const uint64_t piece = len <= (64ull << 20) ? std::max<uint64_t>(len, 16)
+                                              : std::min<uint64_t>(512ull << 20,
+                                                                   std::max<uint64_t>(64ull << 20, (len / 8 + 15) & ~15ull));
+  const uint64_t n_pieces = len ? (len + piece - 1) / piece : 0;
+  if (!sc->host_ev && cudaEventCreateWithFlags(&sc->host_ev, cudaEventDisableTiming) != cudaSuccess) return PAREM_ERR_CUDA;
+  for (int k = 0; k < 2; ++k)
+    if (!sc->copy_st[k] && cudaStreamCreateWithFlags(&sc->copy_st[k], cudaStreamNonBlocking) != cudaSuccess)
+      return PAREM_ERR_CUDA;
+  while (sc->piece_ev.size() < n_pieces) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PAREM_ERR_CUDA;
+    sc->piece_ev.push_back(e);
+  }
+  // the staging buffer is free once the work already queued on the stream is done
+  PAREM_CUDA_TRY(cudaEventRecord(sc->host_ev, st));
+  uint8_t* dtext = static_cast<uint8_t*>(sc->dev_text);
+  for (uint64_t k = 0; k < n_pieces; ++k) {
+    cudaStream_t cs = sc->copy_st[k & 1];
+    if (k < 2) PAREM_CUDA_TRY(cudaStreamWaitEvent(cs, sc->host_ev, 0));
+    const uint64_t off = k * piece, n = std::min(piece, len - off);
+    PAREM_CUDA_TRY(cudaMemcpyAsync(dtext + off, text + off, n, cudaMemcpyHostToDevice, cs));
+    PAREM_CUDA_TRY(cudaEventRecord(sc->piece_ev[k], cs));
+  }
+  const Prepared& P = dfa->host;
+  uint32_t state = P.orig_of[P.start];
+  bool dead = false;
+  uint64_t total = 0, written = 0;
+  uint8_t accepted = P.start >= P.first_accept ? 1 : 0;
+  rc = PAREM_OK;
+  for (uint64_t k = 0; k < n_pieces && !dead; ++k) {
+    const uint64_t off = k * piece, n = std::min(piece, len - off);
+    PAREM_CUDA_TRY(cudaStreamWaitEvent(st, sc->piece_ev[k], 0));
+    parem_match_opts o{};
+    o.start_state = state;
+    o.use_start_state = 1;
+    parem_result r;
+    const bool room = want && written < capacity;
+    const int rk = run_scan(dfa, dtext + off, n, room ? static_cast<uint64_t*>(sc->dev_pos) + written : nullptr,
+                            room ? capacity - written : 0, &o, st, &r, off);
+    if (rk != PAREM_OK && rk != PAREM_ERR_CAPACITY) {
+      rc = rk;
+      break;
+    }
+    total += r.match_count;
+    written += r.n_written;
+    accepted = r.accepted;
+    if (r.final_state == PAREM_NONE) dead = true;
+    else state = r.final_state;
+  }
+  // copies of pieces after a dead end (or an error) may still be in flight
+  for (int k = 0; k < 2; ++k) cudaStreamSynchronize(sc->copy_st[k]);
+  if (rc != PAREM_OK) return rc;
+  out->final_state = dead ? PAREM_NONE : state;
+  out->accepted = dead ? 0 : accepted;
+  out->match_count = total;
+  out->n_written = want ? std::min<uint64_t>(total, capacity) : 0;
   if (want && out->n_written) {
     PAREM_CUDA_TRY(cudaMemcpyAsync(positions, sc->dev_pos, out->n_written * 8, cudaMemcpyDeviceToHost, st));
-    PAREM_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  return rc;
+  PAREM_CUDA_TRY(cudaStreamSynchronize(st));
+  return (want && total > capacity) ? PAREM_ERR_CAPACITY : PAREM_OK;
 }

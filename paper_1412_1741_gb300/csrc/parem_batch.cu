@@ -211,7 +211,7 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
       return rc;
     }
     const Prepared& P = s.dfa->host;
-    if (P.max_cand > 256 && P.n <= 16384) {
+    if (P.n <= 16384 && P.max_cand > kLanes && (P.max_cand > 256 || (P.sync_len > 16 && P.n >= 256))) {
       s.bitmap_words = (P.n + 31) / 32;
       s.spec_bytes = kSpecBytes + (uint32_t)up(8ull * s.bitmap_words, 16) + 512u;
     }
@@ -382,6 +382,7 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     BatchSlot& bs = hslots[si];
     bs.dfa = slots[si].dfa->batch;
     bs.smem_tier = slots[si].smem_tier ? 1u : 0u;
+    bs.grouped = slots[si].dfa->host.max_cand <= kLanes ? 1u : 0u;
     bs.item_begin = pos_k;
     bs.item_end = pos_k + (uint32_t)slots[si].items.size();
     bs.n_chunks = slot_chunks[si];
@@ -413,7 +414,10 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     p.tail = pl.tail;
     p.n_chunks = pl.chunks;
     p.init_state = P.start;
+    // lanes per row of the grouped speculation: the smallest power of two holding the
+    // largest candidate set (used when the slot is grouped)
     p.group = 1;
+    while (p.group < P.max_cand && p.group < kLanes) p.group *= 2;
     p.bitmap_words = slots[slot_of[it.dfa]].bitmap_words;
     p.spec_bytes = spec_bytes;
     p.smem_table_bytes = 0;
@@ -556,7 +560,7 @@ float time_trial(const std::vector<parem_batch_item>& its, uint64_t S, int warps
   cudaEventCreate(&e1);
   float best = 1e30f;
   run_internal(t, st);  // warm-up
-  for (int rep = 0; rep < 2; ++rep) {
+  for (int rep = 0; rep < 1; ++rep) {
     cudaEventRecord(e0, st);
     if (run_internal(t, st) != PAREM_OK) {
       best = 1e30f;
@@ -613,20 +617,28 @@ extern "C" int parem_batch_create(const parem_batch_item* items, uint32_t n_item
         best_s[kv.first] = s0;
         continue;
       }
-      // the DFA's share of the batch's CTAs, in proportion to its bytes
-      const int share = std::max(1, (int)std::lround((double)grid * (double)bytes / (double)all_bytes));
+      // trials on the DFA's first items up to 64 MiB, with the matching share of the batch's
+      // CTAs (the DFA's bytes over all bytes)
+      std::vector<parem_batch_item> sub;
+      uint64_t sub_bytes = 0;
+      for (const auto& it : kv.second) {
+        if (sub_bytes >= (64u << 20)) break;
+        sub.push_back(it);
+        sub_bytes += it.len;
+      }
+      const int share = std::max(1, (int)std::lround((double)grid * (double)sub_bytes / (double)all_bytes));
       // a first trial at the default size teaches the DFA's convergence length
-      float best = time_trial(kv.second, s0, warps, share);
+      float best = time_trial(sub, s0, warps, share);
       uint64_t pick = s0;
       const uint64_t smin = min_row_bytes(kv.first, 8);
       const uint64_t smax = std::max(smin, max_row_bytes(kv.first, kv.first->host.max_cand));
       std::vector<uint64_t> tried{s0};
-      for (double f : {0.25, 0.5, 1.0, 2.0, 4.0, 8.0}) {
+      for (double f : {0.5, 1.0, 2.0, 4.0}) {
         uint64_t S = up((uint64_t)std::llround((double)std::max(s0, smin) * f), kBox);
         S = std::min<uint64_t>(std::max<uint64_t>(S, smin), std::min<uint64_t>(smax, 4u << 20));
         if (std::find(tried.begin(), tried.end(), S) != tried.end()) continue;
         tried.push_back(S);
-        const float ms = time_trial(kv.second, S, warps, share);
+        const float ms = time_trial(sub, S, warps, share);
         if (ms < best) {
           best = ms;
           pick = S;
@@ -670,6 +682,23 @@ extern "C" int parem_batch_results(const parem_batch* batch, parem_result* out) 
     res.match_count = r.count;
     res.n_written = (it.positions && it.capacity) ? std::min<uint64_t>(r.count, it.capacity) : 0;
   }
+  return PAREM_OK;
+}
+
+extern "C" int parem_batch_stats(const parem_batch* batch, parem_stats* out) {
+  if (!batch || !out) return PAREM_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  for (uint32_t k = 0; k < batch->n_items; ++k) {
+    const DevResult& r = batch->host_res[k];
+    out->nonconv_rows += r.nonconv_rows;
+    out->conv_max = std::max(out->conv_max, r.conv_max);
+    out->cycles_spec += r.cyc_spec;
+    out->cycles_main += r.cyc_main;
+    out->cycles_resolve += r.cyc_resolve;
+    out->cycles_bitmap += r.cyc_bitmap;
+    out->cycles_lane += r.cyc_lane;
+  }
+  out->kernels = batch_kernels(batch);
   return PAREM_OK;
 }
 

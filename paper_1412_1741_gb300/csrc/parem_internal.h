@@ -117,6 +117,10 @@ struct DevResult {
   uint32_t progress;         // bumped by long serial steps; device waits time out only
                              // when it has not moved for their whole budget
   uint32_t pad;
+  // SM cycles spent by the chunk-owning warps, summed over chunks: speculation (with slot
+  // maps), main run, resolution (waits, look-back, row records)
+  unsigned long long cyc_spec, cyc_main, cyc_resolve;
+  unsigned long long cyc_bitmap, cyc_lane;  // parts of cyc_spec: bitmap phase, lane phase
 };
 
 // Parameters of one plain scan (one text).
@@ -138,6 +142,7 @@ struct ScanParams {
   uint32_t cand_stride;    // slots per segment in the slot map
   uint32_t serial_fallback;  // rows that did not merge are run from their resolved start
                              // (no slot maps); else every candidate gets a slot-map entry
+  uint64_t pos_base;       // added to every position written (text offset of a piece)
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch
@@ -164,7 +169,7 @@ struct BatchSlot {
   DeviceDfa dfa;           // kBatchDyn copy: u16 class table, u16 column map
   uint32_t smem_tier;      // 1: the table is staged in shared memory
   uint32_t item_begin, item_end;
-  uint32_t pad;
+  uint32_t grouped;        // 1: candidate sets of at most 32 states, grouped speculation
   uint64_t n_chunks;       // chunks of all its items
   uint64_t n_rows;         // rows of all its items
   uint32_t* ticket;        // chunk ticket counter of the slot

@@ -192,8 +192,13 @@ template <int LAYOUT, int ESIZE>
 __device__ uint32_t run_range16(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p, uint64_t len,
                                 uint32_t x, uint32_t dead, uint32_t first_accept, uint32_t* cnt) {
   uint32_t c = 0;
+  const uint4 zero = make_uint4(0, 0, 0, 0);
+  // two vectors in flight ahead of the one being consumed
+  uint4 a = len >= 16 ? ldg16(p) : zero, b = len >= 32 ? ldg16(p + 16) : zero;
   for (uint64_t o = 0; o < len; o += 16) {
-    const uint4 v = ldg16(p + o);
+    const uint4 v = a;
+    a = b;
+    b = o + 48 <= len ? ldg16(p + o + 32) : zero;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       x = tab.next(x, tab.col(byte_of(v, i)));
@@ -304,6 +309,35 @@ struct WarpCtx {
 };
 
 // One chunk (32 rows) of one text: speculation, main run, look-back, row records.
+__device__ __forceinline__ uint4 row_load16(const uint8_t* row, uint32_t pos, uint32_t lim) {
+  return pos + 16 <= lim ? ldg16(row + pos) : make_uint4(0, 0, 0, 0);
+}
+
+// Sequential 16-byte reads of one row of text [0, lim).  With PF, the vector at the reader's
+// position is loaded one step ahead of its use (the kernels for large candidate sets, whose
+// speculation runs long past the staged bytes); without, it is loaded when used (fewer live
+// registers).
+template <bool PF>
+struct RowAhead;
+template <>
+struct RowAhead<true> {
+  uint4 v0;
+  __device__ __forceinline__ void init(const uint8_t* row, uint32_t pos, uint32_t lim) { v0 = row_load16(row, pos, lim); }
+  __device__ __forceinline__ uint4 get(const uint8_t*, uint32_t, uint32_t) const { return v0; }
+  // advance from pos to pos + 16
+  __device__ __forceinline__ void shift(const uint8_t* row, uint32_t pos, uint32_t lim) {
+    v0 = row_load16(row, pos + 16, lim);
+  }
+};
+template <>
+struct RowAhead<false> {
+  __device__ __forceinline__ void init(const uint8_t*, uint32_t, uint32_t) {}
+  __device__ __forceinline__ uint4 get(const uint8_t* row, uint32_t pos, uint32_t lim) const {
+    return row_load16(row, pos, lim);
+  }
+  __device__ __forceinline__ void shift(const uint8_t*, uint32_t, uint32_t) {}
+};
+
 template <int LAYOUT, int ESIZE, int P>
 __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p,
                                            const CUtensorMap* tmap, const uint64_t j) {
@@ -329,6 +363,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   const bool last_row = active && myrow == p.R - 1;
   const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
 
+  const uint32_t clk0 = (uint32_t)clock64();
   // 1. start the TMA pipeline for this chunk
   if (lane == 0) {
     for (uint32_t b = 0; b < issue_first; ++b) {
@@ -346,14 +381,12 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       failed = true;
     }
   }
-  // 16 bytes of row k of this chunk at row offset pos (staged bytes from shared memory)
-  auto read16 = [&](uint32_t k, uint32_t pos) -> uint4 {
-    if (pos < issue_first * kBox) {
-      const uint32_t b = pos / kBox;
-      const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
-      return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
-    }
-    return ldg16(body + (row0 + k) * p.S + pos);
+  // the first bytes of every row of the chunk are already staged in shared memory
+  const uint32_t staged = issue_first * kBox;
+  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 {
+    const uint32_t b = pos / kBox;
+    const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
+    return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
   };
   auto cand_class = [&](uint64_t r) -> uint32_t {
     return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
@@ -391,12 +424,16 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       unsigned live = __ballot_sync(kFull, st != kEmpty);
       bool done = exact || !valid || __popc(live & gmask) <= 1;
       uint32_t pos = 0, outcome = 1;
+      const uint8_t* grow = body + (row0 + (valid ? k : 0u)) * p.S;
+      const uint32_t kk = valid ? k : 0u;
+      RowAhead<false> ra;
+      ra.init(grow, staged, (uint32_t)p.S);
       while (!__all_sync(kFull, done)) {
         if (!done && pos >= cap) {
           done = true;
           outcome = 3;
         }
-        const uint4 v = read16(valid ? k : 0u, pos);
+        const uint4 v = pos < staged ? staged16(kk, pos) : ra.get(grow, pos, (uint32_t)p.S);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -410,7 +447,10 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           const unsigned grp = __match_any_sync(kFull, key);
           if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
         }
-        if (!done) pos += 16;
+        if (!done) {
+          if (pos >= staged) ra.shift(grow, pos, (uint32_t)p.S);
+          pos += 16;
+        }
         live = __ballot_sync(kFull, st != kEmpty);
         if (!done && __popc(live & gmask) <= 1) done = true;
       }
@@ -463,6 +503,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       uint32_t st[P];
       uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
       uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
+      const uint32_t cb0 = (uint32_t)clock64();
       if (big) {
         // More candidates than registers: the warp keeps the candidate set as a bitmap over
         // the states (duplicates merge by construction) until it fits 32 * P registers.
@@ -477,12 +518,16 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         }
         __syncwarp();
         uint32_t cnt = m;
+        const uint8_t* brow = body + r * p.S;
+        RowAhead<(P >= 4)> ra;
+        ra.init(brow, pos > staged ? pos : staged, (uint32_t)p.S);
         for (;;) {
           if (pos >= cap) {
             outcome = 3;
             break;
           }
-          const uint4 v = read16(k, pos);
+          const uint4 v = pos < staged ? staged16(k, pos) : ra.get(brow, pos, (uint32_t)p.S);
+          if (pos >= staged) ra.shift(brow, pos, (uint32_t)p.S);
 #pragma unroll 1
           for (int q = 0; q < 16; ++q) {
             const uint32_t c = tab.col(byte_of(v, q));
@@ -522,6 +567,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           cnt = __reduce_add_sync(kFull, local);
           if (cnt <= 32u * P) break;
         }
+        if (lane == 0) atomicAdd(&p.result->cyc_bitmap, (unsigned long long)((uint32_t)clock64() - cb0));
         if (outcome == 0) {
           // list the surviving states in the hand-over buffer, then load the registers
           uint32_t local = 0;
@@ -560,12 +606,83 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           if ((uint32_t)i * 32u < m) lr |= 1u << i;
         }
       }
+      const uint8_t* wrow = body + r * p.S;
+      RowAhead<(P >= 4)> wa;
+      wa.init(wrow, pos > staged ? pos : staged, (uint32_t)p.S);
       for (; outcome == 0;) {
         if (pos >= cap) {
           outcome = 3;
           break;
         }
-        const uint4 v = read16(k, pos);
+        const uint4 v = pos < staged ? staged16(k, pos) : wa.get(wrow, pos, (uint32_t)p.S);
+        if (pos >= staged) wa.shift(wrow, pos, (uint32_t)p.S);
+        if (p.bitmap_words) {
+          // 16 steps with no merging inside them, then one merge of equal states across all
+          // lanes and registers through the state bitmap, which also packs the survivors
+          // densely into the first registers
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const uint32_t c = tab.col(byte_of(v, q));
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              if ((lr >> i) & 1u) {
+                if (st[i] != kEmpty) {
+                  const uint32_t s2 = tab.next(st[i], c);
+                  st[i] = (s2 == dead) ? kEmpty : s2;
+                }
+              }
+            }
+          }
+          pos += 16;
+          const uint32_t W = p.bitmap_words;
+          uint32_t* bm = bitmaps;
+          for (uint32_t w = lane; w < W; w += 32) bm[w] = 0;
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < P; ++i)
+            if (((lr >> i) & 1u) && st[i] != kEmpty) atomicOr(&bm[st[i] >> 5], 1u << (st[i] & 31u));
+          __syncwarp();
+          uint32_t local = 0;
+          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm[w]);
+          uint32_t incl = local;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(kFull, incl, d);
+            if (lane >= (uint32_t)d) incl += o;
+          }
+          const uint32_t cnt = __shfl_sync(kFull, incl, 31);
+          uint32_t idx = incl - local;
+          uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
+          for (uint32_t w = lane; w < W; w += 32) {
+            uint32_t bits = bm[w];
+            while (bits) {
+              list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
+              bits &= bits - 1;
+            }
+          }
+          __syncwarp();
+          lr = 0;
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const uint32_t slot = (uint32_t)i * 32u + lane;
+            st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
+            if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
+          }
+          __syncwarp();
+          if (cnt <= 1) {
+            outcome = 1;
+            sigma = cnt ? __shfl_sync(kFull, st[0], 0) : dead;
+            break;
+          }
+          if (cnt <= kLaneCand) {
+            // few survivors left: the lane that owns the row finishes them (phase 2b)
+            if (lane < cnt) hand[k * kLaneCand + lane] = (uint16_t)st[0];
+            sigma = cnt;
+            outcome = 2;
+            break;
+          }
+          continue;
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
 #pragma unroll
@@ -657,65 +774,82 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
 
+    const uint32_t cl0 = (uint32_t)clock64();
     // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
     if (__ballot_sync(kFull, my_hand != 0) && !failed) {
       __syncwarp();
-      if (my_hand) {
+      // every lane runs the loop (lanes without survivors idle through it); the survivor
+      // slots it touches are bounded by the warp's largest survivor count, which is uniform,
+      // so slots nobody uses cost nothing
+      {
         uint32_t ls[kLaneCand];
 #pragma unroll
         for (uint32_t i = 0; i < kLaneCand; ++i)
           ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
         uint32_t L = my_hand, pos = my_t;
+        bool busy = my_hand != 0;
+        const uint8_t* lrow = body + (active ? myrow : row0) * p.S;
+        RowAhead<(P >= 4)> la;
+        if (busy) la.init(lrow, pos > staged ? pos : staged, (uint32_t)p.S);
         for (;;) {
-          if (pos >= cap) {
+          if (busy && pos >= cap) {
             my_conv = 0;
             my_t = (uint32_t)p.S;
-            break;
+            busy = false;
           }
-          const uint4 v = read16(lane, pos);
+          const uint32_t lmax = __reduce_max_sync(kFull, busy ? L : 0u);
+          if (lmax == 0) break;
+          const uint4 v = !busy ? make_uint4(0, 0, 0, 0) : pos < staged ? staged16(lane, pos) : la.get(lrow, pos, (uint32_t)p.S);
+          if (busy && pos >= staged) la.shift(lrow, pos, (uint32_t)p.S);
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const uint32_t c = tab.col(byte_of(v, q));
 #pragma unroll
             for (uint32_t i = 0; i < kLaneCand; ++i) {
-              if (i < L && ls[i] != kEmpty) {
-                const uint32_t s2 = tab.next(ls[i], c);
-                ls[i] = (s2 == dead) ? kEmpty : s2;
+              if (i < lmax) {  // warp-uniform
+                if (ls[i] != kEmpty) {
+                  const uint32_t s2 = tab.next(ls[i], c);
+                  ls[i] = (s2 == dead) ? kEmpty : s2;
+                }
               }
             }
           }
           pos += 16;
-#pragma unroll
-          for (uint32_t i = 0; i < kLaneCand; ++i)
-#pragma unroll
-            for (uint32_t jj = i + 1; jj < kLaneCand; ++jj)
-              if (ls[jj] == ls[i]) ls[jj] = kEmpty;
+          // merge equal survivors and compact them to the front
           uint32_t out[kLaneCand];
 #pragma unroll
           for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
           uint32_t np = 0;
 #pragma unroll
           for (uint32_t i = 0; i < kLaneCand; ++i) {
-            const bool keep = ls[i] != kEmpty;
+            if (i < lmax) {
+              bool keep = ls[i] != kEmpty;
 #pragma unroll
-            for (uint32_t qq = 0; qq < kLaneCand; ++qq)
-              if (keep && qq == np) out[qq] = ls[i];
-            np += keep ? 1u : 0u;
+              for (uint32_t jj = 0; jj < i; ++jj)
+                if (ls[jj] == ls[i]) keep = false;
+#pragma unroll
+              for (uint32_t qq = 0; qq < kLaneCand; ++qq)
+                if (qq <= i && keep && qq == np) out[qq] = ls[i];
+              np += keep ? 1u : 0u;
+            }
           }
 #pragma unroll
           for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
-          L = np;
-          if (L <= 1) {
-            my_conv = 1;
-            my_t = pos;
-            my_sigma = L ? ls[0] : dead;
-            break;
+          if (busy) {
+            L = np;
+            if (L <= 1) {
+              my_conv = 1;
+              my_t = pos;
+              my_sigma = L ? ls[0] : dead;
+              busy = false;
+            }
           }
         }
         my_hand = 0;
       }
       __syncwarp();
     }
+    if (lane == 0) atomicAdd(&p.result->cyc_lane, (unsigned long long)((uint32_t)clock64() - cl0));
   }
 
   // convergence statistics for the planner (one update per chunk)
@@ -754,6 +888,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     if (lane == 0) atomicAdd(&p.result->progress, 1u);
   }
 
+  const uint32_t clk1 = (uint32_t)clock64();
   // 4. main run: each lane runs its merged state over the rest of its row from smem,
   //    remembering the first and last 16-byte vectors that contain matches
   uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
@@ -843,6 +978,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   }
   const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
 
+  const uint32_t clk2 = (uint32_t)clock64();
   // 5. the chunk's end state is known now if every row merged
   //    (or if at least its last row did: E_last does not depend on the chunk's start, and
   //    publishing it now keeps chunks with unmerged rows from forming a chain)
@@ -1106,6 +1242,12 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     p.result->final_state = inc.dead ? dead : E_chunk;
     p.result->count = inc.count;
   }
+  if (lane == 0) {
+    // 32-bit cycle differences (a chunk takes far less than 2^32 cycles)
+    atomicAdd(&p.result->cyc_spec, (unsigned long long)(clk1 - clk0));
+    atomicAdd(&p.result->cyc_main, (unsigned long long)(clk2 - clk1));
+    atomicAdd(&p.result->cyc_resolve, (unsigned long long)((uint32_t)clock64() - clk2));
+  }
 }
 
 // Wait (bounded) for stages still in flight before the CTA may release its shared memory.
@@ -1189,7 +1331,7 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         x = tab.next(x, tab.col(byte_of(v, i)));
-        if (x >= A && o < end) p.positions[o++] = gbase + off + (uint64_t)i;
+        if (x >= A && o < end) p.positions[o++] = p.pos_base + gbase + off + (uint64_t)i;
       }
       off += 16;
     }
@@ -1200,12 +1342,12 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         x = tab.next(x, tab.col(byte_of(v, i)));
-        if (x >= A && o < end) p.positions[o++] = gbase + off + (uint64_t)i;
+        if (x >= A && o < end) p.positions[o++] = p.pos_base + gbase + off + (uint64_t)i;
       }
       off += 16;
     } else {
       x = tab.next(x, tab.col(ldg8(rowp + off)));
-      if (x >= A) p.positions[o++] = gbase + off;
+      if (x >= A) p.positions[o++] = p.pos_base + gbase + off;
       off += 1;
     }
   }
@@ -1224,7 +1366,7 @@ __device__ __forceinline__ void emit_row(const Tab<LAYOUT, ESIZE>& tab, const Sc
     uint32_t x = sr.x;
     for (uint64_t i = 0; i < p.h && o < end; ++i) {
       x = tab.next(x, tab.col(ldg8(p.text + i)));
-      if (x >= A) p.positions[o++] = i;
+      if (x >= A) p.positions[o++] = p.pos_base + i;
     }
   } else if (sr.flags & kPreFlag) {
     // matches inside the merged prefix [0, t), replayed from the row's true start
@@ -1236,7 +1378,7 @@ __device__ __forceinline__ void emit_row(const Tab<LAYOUT, ESIZE>& tab, const Sc
     // pass 1 recorded every main-run match of this row
     const uint64_t gbase = p.h + r * p.S;
     const uint32_t* sl = p.slots + r * kRowSlots;
-    for (uint32_t i = 0; o < end; ++i) p.positions[o++] = gbase + sl[i];
+    for (uint32_t i = 0; o < end; ++i) p.positions[o++] = p.pos_base + gbase + sl[i];
     return;
   }
   atomicAdd(&p.result->emit_replays, 1u);
@@ -1296,7 +1438,7 @@ __global__ void k_tiny(const ScanParams p) {
     if (x == D.dead) break;
     x = tab.next(x, tab.col(ldg8(p.text + i)));
     if (x >= D.first_accept) {
-      if (p.positions && cnt < p.capacity) p.positions[cnt] = i;
+      if (p.positions && cnt < p.capacity) p.positions[cnt] = p.pos_base + i;
       ++cnt;
     }
   }
@@ -1357,7 +1499,10 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
       }
       const BatchItem& it = bp.items[lo];
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it.tmap) : "memory");
-      scan_chunk<kBatchDyn, 2, 8>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
+      if (S.grouped)
+        scan_chunk<kBatchDyn, 2, 1>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
+      else
+        scan_chunk<kBatchDyn, 2, 8>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
     }
     __syncthreads();  // every warp is done with this slot's tables
     if (threadIdx.x == 0) {
@@ -1416,7 +1561,7 @@ __global__ void k_batch_tiny(const __grid_constant__ BatchParams bp, const uint3
     const uint32_t c = *reinterpret_cast<const uint16_t*>(D.colmap + 2 * ldg8(p.text + i));
     x = __ldg(reinterpret_cast<const uint16_t*>(D.table + x * D.rowbytes + c));
     if (x >= D.first_accept) {
-      if (p.positions && cnt < p.capacity) p.positions[cnt] = i;
+      if (p.positions && cnt < p.capacity) p.positions[cnt] = p.pos_base + i;
       ++cnt;
     }
   }

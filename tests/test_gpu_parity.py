@@ -55,6 +55,7 @@ def check(torch, spec, text, offset=0, opts=None, positions=True, capacity=None,
         o = opts or pm.MatchOpts()
         if start is not None:
             o.start_state = start
+            o.use_start_state = 1
         got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
     assert got.final_state == want.final_state
     assert got.accepted == want.accepted
@@ -198,6 +199,40 @@ def test_host_buffers(torch):
     got = pm.parem_match_host(load(GATTACA), text, pos)
     assert (got.final_state, got.match_count) == (want.final_state, want.match_count)
     assert np.array_equal(pos[:got.n_written], want.positions)
+
+
+def test_host_buffers_in_pieces(torch):
+    # 200 MiB: the host path copies and scans 64 MiB pieces, each from the state the previous
+    # one ended in; positions of all pieces land in one buffer, in order, with a capacity
+    # that runs out inside a later piece
+    n = 200 << 20
+    text_dev = wl.uniform_text_device(n, 4, torch.device("cuda"), seed=12)
+    host = text_dev.cpu().numpy()
+    dfa = load(GATTACA)
+    ref_pos = torch.full((4096,), -1, dtype=torch.int64, device="cuda")
+    ref = pm.parem_match(dfa, text_dev, ref_pos)
+    assert ref.match_count > 2000
+    for cap in (4096, 1500):
+        pos = np.zeros(cap, np.uint64)
+        got = pm.parem_match_host(dfa, host, pos)
+        assert (got.final_state, got.accepted, got.match_count) == (ref.final_state, ref.accepted, ref.match_count)
+        assert got.n_written == min(cap, ref.match_count)
+        assert np.array_equal(pos[:got.n_written], ref_pos[:got.n_written].cpu().numpy().astype(np.uint64))
+    # a partial DFA (KMP of "GAT" with C undefined) whose run dies in the second piece: the
+    # matches before the death count, nothing after it does
+    t, acc = wl.kmp_dfa([2, 0, 3], 4)
+    t = np.array(t, dtype=np.uint32)
+    t[:, 1] = NONE
+    spec = wl.DfaSpec(t, 0, acc, None, "gat-no-C")
+    host2 = host.copy()
+    head = host2[: 100 << 20]
+    head[head == 1] = 0  # no C before 100 MiB
+    host2[(100 << 20) + 5] = 1
+    want = oracle.scan(spec.table, None, 0, spec.accept, host2[: (100 << 20) + 64])
+    assert want.match_count > 1000 and want.final_state == NONE
+    got = pm.parem_match_host(load(spec), host2, None)
+    assert got.final_state == pm.PAREM_NONE and not got.accepted
+    assert got.match_count == want.match_count
 
 
 @pytest.mark.parametrize("n_states,n_sym,layout", [(400, 140, 3), (450, 200, 4), (150, 4, 0), (700, 30, 1)])
