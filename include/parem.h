@@ -81,7 +81,10 @@ typedef struct {
   uint32_t entry_bytes;     /* 1 (<= 256 compact states) or 2 */
   uint32_t layout;          /* 0: byte-indexed table in shared memory, 1: class-indexed table
                                in shared memory, 2: class-indexed table in global memory (L2);
-                               3 and 4: as 1 and 2 with 2-byte column offsets */
+                               3 and 4: as 1 and 2 with 2-byte column offsets;
+                               6: as 0, plus a table that advances 4 bytes per lookup in the
+                               main run (small DFAs whose bytes 0..K-2 are distinct classes
+                               and whose other bytes share one class) */
   uint32_t table_bytes;     /* bytes of the device transition table */
   uint32_t max_candidates;  /* largest candidate set |img(c) \ {dead}| over classes */
   uint32_t sync_estimate;   /* symbols after which a candidate set has shrunk to one state on

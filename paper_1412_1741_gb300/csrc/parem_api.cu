@@ -247,6 +247,8 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
   D.rowbytes = P.rowbytes;
   D.table_bytes = P.table_bytes;
   D.max_cand = P.max_cand;
+  D.stride_k = P.stride_k;
+  D.stride_off = P.stride_off;
   fill_info(P, &d->info);
   *out = d;
   return PAREM_OK;
@@ -543,7 +545,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
     if (e == cudaSuccess && emit) {
       sc->emitted = true;
       const DevProps props = dev_props(dfa->device);
-      e = launch_emit_dispatch(P.layout, P.esize, p, props.sms * 4, 256, small_smem, stream);
+      e = launch_emit_dispatch(P.layout, P.esize, p, props.sms, 256, small_smem, stream);
     }
   }
   if (e == cudaSuccess && timed && pl.R == 0) e = cudaEventRecord(sc->ev[1], stream);

@@ -16,9 +16,9 @@ constexpr uint32_t kStageBytes = kLanes * kBox;  // 2 KiB: 32 rows x 64 B
 constexpr uint32_t kEmpty = 0xFFFFFFFFu; // an empty candidate register / "no state"
 constexpr uint32_t kNoSlot = 0xFFFFu;    // rank(c, q) when q is not a candidate of class c
 constexpr uint32_t kLaneCand = 8;        // survivors a lane takes over from the warp-wide phase
-// per-warp speculation scratch in shared memory: hand-over lists (32 rows x 8 states, u16)
-// followed by a 32-word compaction buffer
-constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4;
+// per-warp speculation scratch in shared memory: hand-over lists (32 rows x 8 states, u16),
+// a 32-word compaction buffer and five 64-bit phase cycle counters (48 bytes with padding)
+constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4 + 48;
 constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
 constexpr uint32_t kSlotsFlag = 2u;      // SegRec.flags: every main-run match of the row is in its slots
 constexpr uint32_t kPreFlag = 4u;        // SegRec.flags: replay the merged prefix [0, t) from x
@@ -30,7 +30,10 @@ constexpr uint64_t kMaxText = 1ull << 45;
 enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClassSmemW = 3, kClassGlobalW = 4,
                          // batch kernels: class-indexed u16 table with a u16 column map, staged in
                          // shared memory or read from global memory as each DFA requires
-                         kBatchDyn = 5 };
+                         kBatchDyn = 5,
+                         // byte-indexed table plus a 4-symbol-stride table for the main run (small
+                         // DFAs whose bytes 0..K-2 are distinct classes and all others one class)
+                         kByteStride = 6 };
 constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
 // Shared memory of every kernel starts with the column map (512 B reserved) followed by the
 // table at this fixed offset, so table reads use an immediate offset.
@@ -61,6 +64,8 @@ struct Prepared {
   uint32_t max_cand = 0;            // over byte classes
   double mean_cand = 0;
   uint32_t sync_len = 0;            // estimated synchronisation length (symbols), or kNoSync
+  uint32_t stride_k = 0;            // kByteStride: symbols K of the stride table (byte b -> min(b, K-1))
+  uint32_t stride_off = 0;          // kByteStride: offset of the stride table inside `table`
   std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
   std::vector<uint32_t> compact_of; // original -> compact
   std::vector<uint16_t> byte_class; // 256
@@ -86,6 +91,7 @@ struct DeviceDfa {
   const uint16_t* rank;
   uint32_t n, n_classes, first_accept, dead, start;
   uint32_t layout, esize, rowbytes, table_bytes, max_cand;
+  uint32_t stride_k, stride_off;  // kByteStride (see Prepared)
 };
 
 // Per-segment record for the emit pass: the matches of the row lie in the row-relative

@@ -28,3 +28,21 @@ cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStre
 }
 
 }  // namespace parem
+
+namespace parem {
+
+// Small DFAs with the 4-byte stride table (candidate sets of at most 32 states: P = 1).
+cudaError_t scan_byte_stride(const CUtensorMap& tm, const ScanParams& p, int grid, int block, size_t smem,
+                             cudaStream_t s) {
+  return launch_spec_scan<kByteStride, 1, 1>(tm, p, grid, block, smem, s);
+}
+
+cudaError_t emit_byte_stride(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
+  return launch_emit<kByteStride, 1>(p, grid, block, smem, s);
+}
+
+cudaError_t tiny_byte_stride(const ScanParams& p, size_t smem, cudaStream_t s) {
+  return launch_tiny<kByteStride, 1>(p, smem, s);
+}
+
+}  // namespace parem

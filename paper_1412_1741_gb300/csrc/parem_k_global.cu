@@ -36,6 +36,10 @@ cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, co
                                  const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
   switch (layout) {
     case kByteSmem: return scan_byte(esize, P, tm, p, grid, block, smem, s);
+    case kByteStride:
+      // at most 32 compact states, so at most 32 candidates (P == 1); anything else would be
+      // a planning error
+      return P == 1 ? scan_byte_stride(tm, p, grid, block, smem, s) : cudaErrorInvalidValue;
     case kClassSmem: return scan_class(esize, P, tm, p, grid, block, smem, s);
     case kClassSmemW: return scan_class_wide(P, tm, p, grid, block, smem, s);
     case kClassGlobal: return scan_global(0, P, tm, p, grid, block, smem, s);
@@ -47,6 +51,7 @@ cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanPara
                                  size_t smem, cudaStream_t s) {
   switch (layout) {
     case kByteSmem: return emit_byte(esize, p, grid, block, smem, s);
+    case kByteStride: return emit_byte_stride(p, grid, block, smem, s);
     case kClassSmem: return emit_class(esize, p, grid, block, smem, s);
     case kClassSmemW: return emit_class_wide(p, grid, block, smem, s);
     case kClassGlobal: return emit_global(0, p, grid, block, smem, s);
@@ -58,6 +63,7 @@ cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanPara
                                  cudaStream_t s) {
   switch (layout) {
     case kByteSmem: return tiny_byte(esize, p, smem, s);
+    case kByteStride: return tiny_byte_stride(p, smem, s);
     case kClassSmem: return tiny_class(esize, p, smem, s);
     case kClassSmemW: return tiny_class_wide(p, smem, s);
     case kClassGlobal: return tiny_global(0, p, smem, s);

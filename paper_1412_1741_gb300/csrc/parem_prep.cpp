@@ -254,6 +254,37 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
     for (int b = 0; b < 256; ++b) P.colmap[b] = (uint16_t)(P.byte_class[b] * P.esize);
   }
 
+  // Multi-stride table: for a small DFA (<= 32 compact states) whose bytes 0..K-2 are classes
+  // 0..K-2 and whose other bytes all share class K-1, one lookup advances 4 bytes.  Entry for
+  // (state s, bytes b1..b4) at s * K^4 + ((m1 * K + m2) * K + m3) * K + m4, m = min(b, K - 1):
+  // the state after the 4 bytes (5 bits) and how many of the 4 states after each byte are
+  // accepting (3 bits).  The main run of the scan uses it; every other step stays byte-wise.
+  if (P.layout == kByteSmem && n <= 32 && P.n_classes >= 2) {
+    const uint32_t K = P.n_classes;
+    bool ok = K <= 16;
+    for (int b = 0; b < 256 && ok; ++b) ok = P.byte_class[b] == std::min<uint32_t>((uint32_t)b, K - 1);
+    const uint64_t k4 = (uint64_t)K * K * K * K;
+    if (ok && (uint64_t)n * k4 <= (48u << 10)) {
+      const uint32_t off = P.table_bytes;
+      P.table.resize(off + (((uint64_t)n * k4 + 15) & ~15ull), 0);
+      for (uint32_t s = 0; s < n; ++s)
+        for (uint64_t idx = 0; idx < k4; ++idx) {
+          const uint32_t d[4] = {(uint32_t)(idx / (K * K * K)), (uint32_t)(idx / (K * K) % K),
+                                 (uint32_t)(idx / K % K), (uint32_t)(idx % K)};
+          uint32_t x = s, cnt = 0;
+          for (int i = 0; i < 4; ++i) {
+            x = cols[d[i]][x];
+            cnt += x >= P.first_accept ? 1u : 0u;
+          }
+          P.table[off + (uint64_t)s * k4 + idx] = (uint8_t)(x | (cnt << 5));
+        }
+      P.table_bytes = (uint32_t)P.table.size();
+      P.layout = kByteStride;
+      P.stride_k = K;
+      P.stride_off = off;
+    }
+  }
+
   // candidate lists and ranks; list n_classes holds every live state (enumeration mode)
   const uint32_t nl = P.n_classes + 1;
   P.img_off.assign(nl + 1, 0);

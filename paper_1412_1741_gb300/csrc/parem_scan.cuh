@@ -28,6 +28,15 @@
 //     row's offset in the global order.
 #pragma once
 
+// Per-chunk counters in the result word: SM cycles per phase (PAREM_PHASE_STATS) and the
+// convergence statistics the planner learns from (PAREM_CONV_STATS).
+#ifndef PAREM_PHASE_STATS
+#define PAREM_PHASE_STATS 1
+#endif
+#ifndef PAREM_CONV_STATS
+#define PAREM_CONV_STATS 1
+#endif
+
 #include <cstdint>
 
 #include "parem_internal.h"
@@ -116,7 +125,9 @@ __device__ __forceinline__ uint32_t read_progress(const DevResult* r) {
 }
 
 // A device wait gives up when its budget has passed with no serial progress anywhere in the
-// scan: *t0 and *seen restart while the progress word moves.
+// scan: *t0 and *seen restart while the progress word moves.  *seen starts as kEmpty ("not
+// read yet"), so a wait that ends within its budget never reads the progress word; the first
+// expiry reads it and grants one more budget.
 __device__ __forceinline__ bool wait_expired(const DevResult* r, uint64_t budget, long long* t0, uint32_t* seen) {
   if ((uint64_t)(clock64() - *t0) <= budget) return false;
   const uint32_t pr = read_progress(r);
@@ -135,7 +146,7 @@ __device__ __forceinline__ bool wait_expired(const DevResult* r, uint64_t budget
 // ---------------------------------------------------------------------------------------
 template <int LAYOUT, int ESIZE>
 struct Tab {
-  static constexpr bool kByte = LAYOUT == kByteSmem;
+  static constexpr bool kByte = LAYOUT == kByteSmem || LAYOUT == kByteStride;
   static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW;
   static constexpr bool kDyn = LAYOUT == kBatchDyn;
   static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW || LAYOUT == kBatchDyn;
@@ -306,7 +317,25 @@ struct WarpCtx {
   uint32_t* bitmaps;    // candidate bitmaps and state list (bitmap phase)
   uint32_t phase_bits;  // expected parity of each stage barrier
   uint32_t pending;     // stages issued and not yet waited
+  // SM cycles per phase, kept by lane 0 in the warp's shared scratch: speculation, main run,
+  // resolution, bitmap, lane phase; summed over chunks, added to the result word by flush_cycles
+  unsigned long long* cyc;
 };
+
+__device__ __forceinline__ void flush_cycles(WarpCtx& wc, DevResult* r) {
+#if PAREM_PHASE_STATS
+  if (wc.lane == 0) {
+    if (wc.cyc[0] | wc.cyc[1] | wc.cyc[2]) {
+      atomicAdd(&r->cyc_spec, wc.cyc[0]);
+      atomicAdd(&r->cyc_main, wc.cyc[1]);
+      atomicAdd(&r->cyc_resolve, wc.cyc[2]);
+      if (wc.cyc[3]) atomicAdd(&r->cyc_bitmap, wc.cyc[3]);
+      if (wc.cyc[4]) atomicAdd(&r->cyc_lane, wc.cyc[4]);
+    }
+    for (int i = 0; i < 5; ++i) wc.cyc[i] = 0;
+  }
+#endif
+}
 
 // One chunk (32 rows) of one text: speculation, main run, look-back, row records.
 __device__ __forceinline__ uint4 row_load16(const uint8_t* row, uint32_t pos, uint32_t lim) {
@@ -363,7 +392,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   const bool last_row = active && myrow == p.R - 1;
   const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
 
+#if PAREM_PHASE_STATS
   const uint32_t clk0 = (uint32_t)clock64();
+#endif
   // 1. start the TMA pipeline for this chunk
   if (lane == 0) {
     for (uint32_t b = 0; b < issue_first; ++b) {
@@ -503,7 +534,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       uint32_t st[P];
       uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
       uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
+#if PAREM_PHASE_STATS
       const uint32_t cb0 = (uint32_t)clock64();
+#endif
       if (big) {
         // More candidates than registers: the warp keeps the candidate set as a bitmap over
         // the states (duplicates merge by construction) until it fits 32 * P registers.
@@ -567,7 +600,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           cnt = __reduce_add_sync(kFull, local);
           if (cnt <= 32u * P) break;
         }
-        if (lane == 0) atomicAdd(&p.result->cyc_bitmap, (unsigned long long)((uint32_t)clock64() - cb0));
+#if PAREM_PHASE_STATS
+        if (lane == 0) wc.cyc[3] += (uint32_t)clock64() - cb0;
+#endif
         if (outcome == 0) {
           // list the surviving states in the hand-over buffer, then load the registers
           uint32_t local = 0;
@@ -774,7 +809,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
 
+#if PAREM_PHASE_STATS
     const uint32_t cl0 = (uint32_t)clock64();
+#endif
     // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
     if (__ballot_sync(kFull, my_hand != 0) && !failed) {
       __syncwarp();
@@ -849,9 +886,12 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
       __syncwarp();
     }
-    if (lane == 0) atomicAdd(&p.result->cyc_lane, (unsigned long long)((uint32_t)clock64() - cl0));
+#if PAREM_PHASE_STATS
+    if (lane == 0) wc.cyc[4] += (uint32_t)clock64() - cl0;
+#endif
   }
 
+#if PAREM_CONV_STATS
   // convergence statistics for the planner (one update per chunk)
   {
     const unsigned nc = __ballot_sync(kFull, active && !my_conv);
@@ -863,6 +903,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       if (tmax) atomicMax(&p.result->conv_max, tmax);
     }
   }
+#endif
 
   // 3. slot maps of rows whose candidates did not merge (rare): every candidate runs
   //    the whole row (and the tail on the last row), lanes over candidates
@@ -888,7 +929,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     if (lane == 0) atomicAdd(&p.result->progress, 1u);
   }
 
+#if PAREM_PHASE_STATS
   const uint32_t clk1 = (uint32_t)clock64();
+#endif
   // 4. main run: each lane runs its merged state over the rest of its row from smem,
   //    remembering the first and last 16-byte vectors that contain matches
   uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
@@ -926,10 +969,27 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         const uint32_t col = col0 + i * 16u;
         if (col >= my_t) {
           const uint32_t mu0 = mu, s0 = s;
+          if constexpr (LAYOUT == kByteStride) {
+            // four bytes per lookup: the stride table holds the state after them and how
+            // many of the four steps end in an accepting state
+            const uint32_t K = D.stride_k, km = K - 1, k4 = K * K * K * K;
+            const uint8_t* stab = sm + kTableOff + D.stride_off;
+            const uint32_t ws[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            s = tab.next(s, tab.col(byte_of(v[i], q)));
-            mu += (s >= A);
+            for (int g = 0; g < 4; ++g) {
+              const uint32_t w = ws[g];
+              const uint32_t m0 = min(w & 0xFFu, km), m1 = min((w >> 8) & 0xFFu, km);
+              const uint32_t m2 = min((w >> 16) & 0xFFu, km), m3 = min(w >> 24, km);
+              const uint32_t e = stab[s * k4 + ((m0 * K + m1) * K + m2) * K + m3];
+              s = e & 31u;
+              mu += e >> 5;
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              s = tab.next(s, tab.col(byte_of(v[i], q)));
+              mu += (s >= A);
+            }
           }
           if (mu != mu0) {
             if (fv == kEmpty) {
@@ -978,7 +1038,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   }
   const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
 
+#if PAREM_PHASE_STATS
   const uint32_t clk2 = (uint32_t)clock64();
+#endif
   // 5. the chunk's end state is known now if every row merged
   //    (or if at least its last row did: E_last does not depend on the chunk's start, and
   //    publishing it now keeps chunks with unmerged rows from forming a chain)
@@ -1015,7 +1077,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     unsigned long long w = 0;
     if (lane == 0) {
       long long t0 = clock64();
-      uint32_t seen = read_progress(p.result);
+      uint32_t seen = kEmpty;
       for (;;) {
         w = ld_acquire(&p.status[j - 1]);
         if ((w >> 62) != 0) break;
@@ -1146,7 +1208,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       unsigned inc = 0;
       uint32_t limit = 31;
       long long t0 = clock64();
-      uint32_t seen = read_progress(p.result);
+      uint32_t seen = kEmpty;
       for (;;) {
         w = idx >= 0 ? ld_acquire(&p.status[idx]) : ((unsigned long long)kFlagInclusive << 62);
         const uint32_t flag = (uint32_t)(w >> 62);
@@ -1242,12 +1304,14 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     p.result->final_state = inc.dead ? dead : E_chunk;
     p.result->count = inc.count;
   }
+#if PAREM_PHASE_STATS
   if (lane == 0) {
     // 32-bit cycle differences (a chunk takes far less than 2^32 cycles)
-    atomicAdd(&p.result->cyc_spec, (unsigned long long)(clk1 - clk0));
-    atomicAdd(&p.result->cyc_main, (unsigned long long)(clk2 - clk1));
-    atomicAdd(&p.result->cyc_resolve, (unsigned long long)((uint32_t)clock64() - clk2));
+    wc.cyc[0] += clk1 - clk0;
+    wc.cyc[1] += clk2 - clk1;
+    wc.cyc[2] += (uint32_t)clock64() - clk2;
   }
+#endif
 }
 
 // Wait (bounded) for stages still in flight before the CTA may release its shared memory.
@@ -1287,6 +1351,9 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
   wc.bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
   wc.phase_bits = 0;
   wc.pending = 0;
+  wc.cyc = reinterpret_cast<unsigned long long*>(sm + spec0 + kLanes * kLaneCand * 2 + kLanes * 4);
+  if (lane == 0)
+    for (int i = 0; i < 5; ++i) wc.cyc[i] = 0;
   if (lane == 0) {
     for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + wc.bar0 + 8 * s), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1305,6 +1372,7 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
     if ((uint64_t)ticket >= p.n_chunks) break;
     scan_chunk<LAYOUT, ESIZE, P>(wc, tab, p, &tmap, ticket);
   }
+  flush_cycles(wc, p.result);
   drain_stages(wc, p.wait_budget);
 }
 
@@ -1400,7 +1468,7 @@ __device__ __forceinline__ void emit_row(const Tab<LAYOUT, ESIZE>& tab, const Sc
 }
 
 template <int LAYOUT, int ESIZE>
-__global__ void __launch_bounds__(256) k_emit(const ScanParams p) {
+__global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
   const DeviceDfa& D = p.dfa;
@@ -1471,6 +1539,9 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
   wc.bitmaps = reinterpret_cast<uint32_t*>(sm + spec0 + kSpecBytes);
   wc.phase_bits = 0;
   wc.pending = 0;
+  wc.cyc = reinterpret_cast<unsigned long long*>(sm + spec0 + kLanes * kLaneCand * 2 + kLanes * 4);
+  if (lane == 0)
+    for (int i = 0; i < 5; ++i) wc.cyc[i] = 0;
   if (lane == 0) {
     for (uint32_t s = 0; s < kStages; ++s) mbar_init(smem_u32(sm + wc.bar0 + 8 * s), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1503,6 +1574,7 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
         scan_chunk<kBatchDyn, 2, 1>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
       else
         scan_chunk<kBatchDyn, 2, 8>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
+      flush_cycles(wc, it.p.result);  // items differ from chunk to chunk
     }
     __syncthreads();  // every warp is done with this slot's tables
     if (threadIdx.x == 0) {
@@ -1587,7 +1659,20 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
   auto kern = k_emit<LAYOUT, ESIZE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, block, smem, stream>>>(p);
+  // One thread per row: the block size that keeps the most threads resident (the table in
+  // shared memory is per block, so larger blocks share it among more rows), one wave of
+  // resident blocks.  `grid` carries the SM count and `block` the smallest block size.
+  int best_threads = 0, best_block = block, best_blocks = 1;
+  for (int b = block; b <= 1024; b *= 2) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, b, smem) != cudaSuccess) continue;
+    if (nb * b > best_threads) {
+      best_threads = nb * b;
+      best_block = b;
+      best_blocks = nb;
+    }
+  }
+  kern<<<grid * best_blocks, best_block, smem, stream>>>(p);
   return cudaGetLastError();
 }
 

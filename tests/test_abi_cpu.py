@@ -48,8 +48,11 @@ def test_strerror_and_version(lib):
 def test_prepare_info_of_the_workload_dfas(lib):
     g = wl.gattaca_dfa()
     i = pm.parem_prepare_info(g.table, g.byte_to_symbol, g.start, g.accept)
-    # bytes >= 4 are outside {A,C,G,T}: a dead state is added; a tiny table is byte-indexed
-    assert i.has_dead and i.compact_states == 9 and i.layout == 0 and i.entry_bytes == 1
+    # bytes >= 4 are outside {A,C,G,T}: a dead state is added; a tiny table is byte-indexed,
+    # and with bytes 0..3 its own classes and all others one class it gets the 4-byte stride
+    # table: 9 states x 5^4 one-byte entries after the 9 x 256 byte table
+    assert i.has_dead and i.compact_states == 9 and i.layout == 6 and i.entry_bytes == 1
+    assert i.n_classes == 5 and 9 * 256 + 9 * 625 <= i.table_bytes <= 9 * 260 + 9 * 625 + 32
     # img of each symbol of the KMP automaton of GATTACA: A->{0,2,5,7}, C->{0,6}, G->{1}, T->{0,3,4}
     assert i.max_candidates == 4
     d = wl.dense_dfa()
@@ -67,6 +70,7 @@ def test_candidate_set_sizes_match_the_paper_example(lib):
     p = wl.parallel_dfa()
     # a complete DFA over its 5 symbols; identity byte map leaves bytes >= 5 outside
     i = pm.parem_prepare_info(p.table, None, 0, p.accept)
+    assert i.layout == 6 and i.n_classes == 6
     # img(l) = {0,5,6,8} is the largest image (Section II-C)
     assert i.max_candidates == 4
 

@@ -201,6 +201,23 @@ def test_host_buffers(torch):
     assert np.array_equal(pos[:got.n_written], want.positions)
 
 
+@pytest.mark.parametrize("n_sym,n_states", [(1, 3), (2, 5), (3, 17), (4, 31), (5, 12)])
+def test_four_byte_stride_table(torch, n_sym, n_states):
+    # small DFAs over bytes 0..n_sym-1 (every other byte is outside the alphabet): the main
+    # run advances 4 bytes per lookup (layout 6); texts include outside bytes and lengths
+    # that are not multiples of 4 or 16
+    t, acc = wl.random_dfa(n_states, n_sym, max(1, n_states // 4), seed=100 + n_states)
+    spec = wl.DfaSpec(t, 0, acc, None, f"stride{n_sym}x{n_states}")
+    assert pm.parem_prepare_info(t, None, 0, acc).layout == 6
+    rng = np.random.default_rng(n_states)
+    text = rng.integers(0, n_sym, size=300_003).astype(np.uint8)
+    text[rng.random(text.size) < 0.001] = 200  # outside bytes kill the run
+    check(torch, spec, text, offset=3, opts=pm.MatchOpts(segment_bytes=1024))
+    check(torch, spec, text[:77_777], opts=pm.MatchOpts(segment_bytes=128))
+    clean = rng.integers(0, n_sym, size=250_001).astype(np.uint8)
+    check(torch, spec, clean, offset=5)
+
+
 def test_host_buffers_in_pieces(torch):
     # 200 MiB: the host path copies and scans 64 MiB pieces, each from the state the previous
     # one ended in; positions of all pieces land in one buffer, in order, with a capacity
