@@ -90,6 +90,27 @@ def profiled_traffic(config, n, plan):
 
 
 # ---------------------------------------------------------------------------------------
+# multi-rank timing: every rank scans its own data (weak scaling); the job's time is the
+# slowest rank's, and the job's throughput counts the bytes of all ranks
+# ---------------------------------------------------------------------------------------
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The largest of the ranks' times (ms); the value itself on one rank (dist None)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(bytes_per_rank_step: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: the bytes every rank scanned in every step over the slowest
+    rank's time (GB/s, 1e9)."""
+    return bytes_per_rank_step * world * steps / (max_ms / 1e3) / 1e9
+
+
+# ---------------------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------------------
 def make_workload(config, device, seed_shift=0):
@@ -289,10 +310,7 @@ def run_batch(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     step_ms = sorted(a.elapsed_time(b) for a, b in evs)
     res = batch.results()
     # plain: one parem_match per text on the same stream (same texts, same results)
@@ -309,7 +327,7 @@ def run_batch(args, rank, world, local_rank):
             dist.barrier()
             dist.destroy_process_group()
         return
-    value = total * world * args.steps / (total_ms / 1e3) / 1e9
+    value = job_gbs(total, world, args.steps, total_ms)
     peak, peak_kind = measured_peaks()
     achieved = total / (step_ms[len(step_ms) // 2] / 1e3) / 1e9
     segs = batch.segments()
@@ -481,12 +499,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     step_ms = sorted(a.elapsed_time(b) for a, b in step_ev)
-    value = n * world * args.steps / (total_ms / 1e3) / 1e9
+    value = job_gbs(n, world, args.steps, total_ms)
     line = None
     if rank == 0:
         peak, peak_kind = measured_peaks()
