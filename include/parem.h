@@ -84,7 +84,10 @@ typedef struct {
                                3 and 4: as 1 and 2 with 2-byte column offsets;
                                6: as 0, plus a table that advances 4 bytes per lookup in the
                                main run (small DFAs whose bytes 0..K-2 are distinct classes
-                               and whose other bytes share one class) */
+                               and whose other bytes share one class);
+                               7: class table in shared memory whose column is computed from
+                               the byte (all bytes outside one ASCII window of at most 64
+                               values and one extra byte share a class) */
   uint32_t table_bytes;     /* bytes of the device transition table */
   uint32_t max_candidates;  /* largest candidate set |img(c) \ {dead}| over classes */
   uint32_t sync_estimate;   /* symbols after which a candidate set has shrunk to one state on

@@ -249,6 +249,7 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
   D.max_cand = P.max_cand;
   D.stride_k = P.stride_k;
   D.stride_off = P.stride_off;
+  D.win = P.win;
   fill_info(P, &d->info);
   *out = d;
   return PAREM_OK;

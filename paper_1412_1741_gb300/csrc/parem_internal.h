@@ -33,7 +33,10 @@ enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClass
                          kBatchDyn = 5,
                          // byte-indexed table plus a 4-symbol-stride table for the main run (small
                          // DFAs whose bytes 0..K-2 are distinct classes and all others one class)
-                         kByteStride = 6 };
+                         kByteStride = 6,
+                         // class table in shared memory whose columns are computed from the byte:
+                         // bytes [lo, lo + w) -> columns 2.., byte xb -> column 1, others column 0
+                         kClassWin = 7 };
 constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
 // Shared memory of every kernel starts with the column map (512 B reserved) followed by the
 // table at this fixed offset, so table reads use an immediate offset.
@@ -66,6 +69,7 @@ struct Prepared {
   uint32_t sync_len = 0;            // estimated synchronisation length (symbols), or kNoSync
   uint32_t stride_k = 0;            // kByteStride: symbols K of the stride table (byte b -> min(b, K-1))
   uint32_t stride_off = 0;          // kByteStride: offset of the stride table inside `table`
+  uint32_t win = 0;                 // kClassWin: lo | w << 8 | xb << 16
   std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
   std::vector<uint32_t> compact_of; // original -> compact
   std::vector<uint16_t> byte_class; // 256
@@ -92,6 +96,7 @@ struct DeviceDfa {
   uint32_t n, n_classes, first_accept, dead, start;
   uint32_t layout, esize, rowbytes, table_bytes, max_cand;
   uint32_t stride_k, stride_off;  // kByteStride (see Prepared)
+  uint32_t win;                   // kClassWin (see Prepared)
 };
 
 // Per-segment record for the emit pass: the matches of the row lie in the row-relative

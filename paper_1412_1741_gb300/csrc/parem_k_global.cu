@@ -36,6 +36,7 @@ cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, co
                                  const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
   switch (layout) {
     case kByteSmem: return scan_byte(esize, P, tm, p, grid, block, smem, s);
+    case kClassWin: return scan_win(esize, P, tm, p, grid, block, smem, s);
     case kByteStride:
       // at most 32 compact states, so at most 32 candidates (P == 1); anything else would be
       // a planning error
@@ -52,6 +53,7 @@ cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return emit_byte(esize, p, grid, block, smem, s);
     case kByteStride: return emit_byte_stride(p, grid, block, smem, s);
+    case kClassWin: return emit_win(esize, p, grid, block, smem, s);
     case kClassSmem: return emit_class(esize, p, grid, block, smem, s);
     case kClassSmemW: return emit_class_wide(p, grid, block, smem, s);
     case kClassGlobal: return emit_global(0, p, grid, block, smem, s);
@@ -64,6 +66,7 @@ cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return tiny_byte(esize, p, smem, s);
     case kByteStride: return tiny_byte_stride(p, smem, s);
+    case kClassWin: return tiny_win(esize, p, smem, s);
     case kClassSmem: return tiny_class(esize, p, smem, s);
     case kClassSmemW: return tiny_class_wide(p, smem, s);
     case kClassGlobal: return tiny_global(0, p, smem, s);

@@ -85,6 +85,10 @@ cudaError_t scan_byte_stride(const CUtensorMap& tm, const ScanParams& p, int gri
                              cudaStream_t s);
 cudaError_t emit_byte_stride(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_byte_stride(const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t scan_win(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid, int block,
+                     size_t smem, cudaStream_t s);
+cudaError_t emit_win(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t tiny_win(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class_wide(const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s);

@@ -254,6 +254,57 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
     for (int b = 0; b < 256; ++b) P.colmap[b] = (uint16_t)(P.byte_class[b] * P.esize);
   }
 
+  // Computed columns: when every byte outside one window [lo, lo + w) of ASCII (w <= 64) and
+  // one extra byte xb shares a single class, the column of a byte is arithmetic (window byte
+  // -> 2 + b - lo, xb -> 1, any other byte -> 0), so the scan needs no column-map lookup per
+  // byte.  The table then has w + 2 columns (each window byte its own, even where classes
+  // repeat); it must fit shared memory.
+  if (P.layout != kByteSmem && P.n_classes >= 2) {
+    std::vector<uint32_t> freq(P.n_classes, 0);
+    for (int b = 0; b < 256; ++b) freq[P.byte_class[b]]++;
+    uint32_t other = 0;
+    for (uint32_t c = 1; c < P.n_classes; ++c)
+      if (freq[c] > freq[other]) other = c;
+    std::vector<int> B;
+    int other_byte = -1;
+    for (int b = 0; b < 256; ++b) {
+      if (P.byte_class[b] != other) B.push_back(b);
+      else if (other_byte < 0) other_byte = b;
+    }
+    int lo = -1, w = 0, xb = other_byte;
+    auto fits = [](int l, int h) { return l >= 0 && h < 128 && h - l + 1 <= 64; };
+    if (!B.empty() && fits(B.front(), B.back())) {
+      lo = B.front();
+      w = B.back() - lo + 1;
+    } else if (B.size() >= 2 && fits(B[1], B.back())) {
+      lo = B[1];
+      w = B.back() - lo + 1;
+      xb = B.front();
+    } else if (B.size() >= 2 && fits(B.front(), B[B.size() - 2])) {
+      lo = B.front();
+      w = B[B.size() - 2] - lo + 1;
+      xb = B.back();
+    }
+    const uint32_t rb_win = row_pitch((uint32_t)w + 2, P.esize);
+    if (lo >= 0 && xb >= 0 && (uint64_t)n * rb_win <= smem_table_budget) {
+      P.layout = kClassWin;
+      P.rowbytes = rb_win;
+      P.table_bytes = (uint32_t)(((uint64_t)n * rb_win + 15) & ~15ull);
+      P.table.assign(P.table_bytes, 0);
+      auto column_of = [&](int b) -> uint32_t {
+        if (b >= lo && b < lo + w) return 2u + (uint32_t)(b - lo);
+        return b == xb ? 1u : 0u;
+      };
+      std::vector<int> rep(w + 2, other_byte);
+      rep[1] = xb;
+      for (int i = 0; i < w; ++i) rep[2 + i] = lo + i;
+      for (uint32_t c = 0; c < (uint32_t)w + 2; ++c)
+        for (uint32_t s = 0; s < n; ++s) put(s, c * P.esize, cols[P.byte_class[rep[c]]][s]);
+      for (int b = 0; b < 256; ++b) P.colmap[b] = (uint16_t)(column_of(b) * P.esize);
+      P.win = (uint32_t)lo | ((uint32_t)w << 8) | ((uint32_t)xb << 16);
+    }
+  }
+
   // Multi-stride table: for a small DFA (<= 32 compact states) whose bytes 0..K-2 are classes
   // 0..K-2 and whose other bytes all share class K-1, one lookup advances 4 bytes.  Entry for
   // (state s, bytes b1..b4) at s * K^4 + ((m1 * K + m2) * K + m3) * K + m4, m = min(b, K - 1):

@@ -218,6 +218,28 @@ def test_four_byte_stride_table(torch, n_sym, n_states):
     check(torch, spec, clean, offset=5)
 
 
+@pytest.mark.parametrize("extra", [32, 200, None])
+def test_computed_columns(torch, extra):
+    # bytes 97..122 are symbols 0..25 and one extra byte (below or above 128) symbol 26; all
+    # other bytes are outside the alphabet: layout 7 computes the column from the byte.
+    # Texts draw every byte value so the in-register column arithmetic sees them all.
+    n_sym = 27 if extra is not None else 26
+    t, acc = wl.random_dfa(600, n_sym, 60, seed=31 + (extra or 0))
+    b2s = np.full(256, pm.PAREM_NONE16, np.uint16)
+    b2s[97:123] = np.arange(26)
+    if extra is not None:
+        b2s[extra] = 26
+    spec = wl.DfaSpec(t, 0, acc, b2s, f"win{extra}")
+    assert pm.parem_prepare_info(t, b2s, 0, acc).layout == 7
+    rng = np.random.default_rng(7)
+    letters = rng.integers(97, 123, size=400_000).astype(np.uint8)
+    noise = rng.random(letters.size)
+    letters[noise < 0.02] = extra if extra is not None else 97
+    letters[noise > 0.99995] = rng.integers(0, 256, size=int((noise > 0.99995).sum())).astype(np.uint8)
+    check(torch, spec, letters, offset=9, opts=pm.MatchOpts(segment_bytes=4096))
+    check(torch, spec, rng.integers(0, 256, size=50_001).astype(np.uint8), opts=pm.MatchOpts(segment_bytes=256))
+
+
 def test_host_buffers_in_pieces(torch):
     # 200 MiB: the host path copies and scans 64 MiB pieces, each from the state the previous
     # one ended in; positions of all pieces land in one buffer, in order, with a capacity
@@ -252,7 +274,8 @@ def test_host_buffers_in_pieces(torch):
     assert got.match_count == want.match_count
 
 
-@pytest.mark.parametrize("n_states,n_sym,layout", [(400, 140, 3), (450, 200, 4), (150, 4, 0), (700, 30, 1)])
+@pytest.mark.parametrize("n_states,n_sym,layout", [(400, 140, 3), (450, 200, 4), (150, 4, 0), (700, 100, 1),
+                                                   (700, 30, 7), (500, 60, 7)])
 def test_table_layouts_and_register_counts(torch, n_states, n_sym, layout):
     t, acc = wl.random_dfa(n_states, n_sym, max(1, n_states // 10), seed=n_states + n_sym)
     spec = wl.DfaSpec(t, 0, acc, None, f"rand{n_states}x{n_sym}")
