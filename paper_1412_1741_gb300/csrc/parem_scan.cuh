@@ -155,13 +155,19 @@ struct Tab {
   const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
   uint32_t smem_tier;      // kBatchDyn: 1 when the table is staged in shared memory
-  uint32_t win;            // kClassWin: lo | w << 8 | xb << 16
+  uint32_t win_lo, win_w, win_xb;  // kClassWin: window [lo, lo + w) and the extra byte
 
+  __device__ __forceinline__ void set_win(uint32_t win) {
+    win_lo = win & 0xFFu;
+    win_w = (win >> 8) & 0xFFu;
+    win_xb = win >> 16;
+  }
   __device__ __forceinline__ uint32_t col(uint32_t b) const {
     if (kByte) return b * ESIZE;
     if (kWin) {
-      const uint32_t d = b - (win & 0xFFu);
-      const uint32_t c = d < ((win >> 8) & 0xFFu) ? d + 2u : (b == (win >> 16) ? 1u : 0u);
+      // a few integer operations instead of a column-map read from shared memory
+      const uint32_t d = b - win_lo;
+      const uint32_t c = d < win_w ? d + 2u : (uint32_t)(b == win_xb);
       return c * ESIZE;
     }
     if (kWide) return *reinterpret_cast<const uint16_t*>(sm + 2 * b);
@@ -177,29 +183,6 @@ struct Tab {
                       : (uint32_t)*reinterpret_cast<const uint16_t*>(sm + kTableOff + o);
   }
 };
-
-// kClassWin: the column offsets of the 4 bytes of x at once (SWAR): a byte b in the window
-// [lo, lo + w) (lo + w <= 128, w <= 64) gets 2 + b - lo, the extra byte xb gets 1, any other
-// byte 0; times esize.  A byte of the window test carries into its own bit 7 only.
-// 0xFF in every byte whose bit 7 is set, 0 elsewhere (x has no other bits set): each such
-// byte becomes 0x01, and 0x01 * 0xFF = 0xFF stays within its byte
-__device__ __forceinline__ uint32_t sign_bytes(uint32_t x) { return (x >> 7) * 0xFFu; }
-
-__device__ __forceinline__ uint32_t win_cols4(uint32_t x, uint32_t win, uint32_t esize) {
-  const uint32_t R = 0x01010101u;
-  const uint32_t lo = win & 0xFFu, w = (win >> 8) & 0xFFu, xb = win >> 16;
-  const uint32_t x7 = x & 0x7F7F7F7Fu;
-  const uint32_t a = x7 + (0x80u - lo) * R;             // bit 7: (b & 0x7F) >= lo
-  const uint32_t bq = x7 + (0x80u - lo - w) * R;        // bit 7: (b & 0x7F) >= lo + w
-  const uint32_t in = a & ~(bq | x) & 0x80808080u;      // in the window, and b < 128
-  const uint32_t mw = sign_bytes(in);                   // 0xFF where in the window
-  const uint32_t vw = (a & 0x7F7F7F7Fu) + 2u * R;       // 2 + b - lo
-  const uint32_t z = x ^ (xb * R);
-  const uint32_t e = ~(((z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | z) & 0x80808080u;  // b == xb
-  const uint32_t me = sign_bytes(e);
-  const uint32_t c = (vw & mw) | (R & me & ~mw);
-  return esize == 2 ? c << 1 : c;
-}
 
 // Stage the column map and (shared layouts) the table into shared memory.
 template <int LAYOUT, int ESIZE>
@@ -1014,18 +997,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
               s = e & 31u;
               mu += e >> 5;
             }
-          } else if constexpr (LAYOUT == kClassWin) {
-            // the 16 column offsets at once, no column-map reads
-            uint4 cv;
-            cv.x = win_cols4(v[i].x, tab.win, ESIZE);
-            cv.y = win_cols4(v[i].y, tab.win, ESIZE);
-            cv.z = win_cols4(v[i].z, tab.win, ESIZE);
-            cv.w = win_cols4(v[i].w, tab.win, ESIZE);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              s = tab.next(s, byte_of(cv, q));
-              mu += (s >= A);
-            }
           } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -1407,7 +1378,7 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
   tab.gtable = p.dfa.table;
   tab.rowbytes = p.dfa.rowbytes;
   tab.smem_tier = 1;
-  tab.win = p.dfa.win;
+  tab.set_win(p.dfa.win);
   for (;;) {
     uint32_t ticket = 0;
     if (lane == 0) ticket = read_error(p.result) ? 0xFFFFFFFFu : atomicAdd(p.ticket, 1u);
@@ -1522,7 +1493,7 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
   tab.smem_tier = 1;
-  tab.win = p.dfa.win;
+  tab.set_win(p.dfa.win);
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
        r += (uint64_t)gridDim.x * blockDim.x)
     emit_row<LAYOUT, ESIZE>(tab, p, r);
@@ -1544,7 +1515,7 @@ __global__ void k_tiny(const ScanParams p) {
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
   tab.smem_tier = 1;
-  tab.win = p.dfa.win;
+  tab.set_win(p.dfa.win);
   uint32_t x = p.init_state;
   uint64_t cnt = 0;
   for (uint64_t i = 0; i < p.n; ++i) {
@@ -1602,7 +1573,7 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
     tab.gtable = S.dfa.table;
     tab.rowbytes = S.dfa.rowbytes;
     tab.smem_tier = S.smem_tier;
-    tab.win = 0;
+    tab.set_win(0);
     for (;;) {
       uint32_t ticket = 0;
       if (lane == 0) ticket = atomicAdd(S.ticket, 1u);
