@@ -25,7 +25,7 @@
  *     the dead state (the run has met an undefined transition or a byte outside the
  *     alphabet).
  *
- * Semantics (readings of the paper, see the oracle and the design doc)
+ * Semantics (readings of the paper, the same as the CPU oracle's)
  *   - A transition entry PAREM_NONE is undefined ("Tt[q][c] in Q" fails in Algorithm 1);
  *     a byte whose symbol is PAREM_NONE16 is outside the alphabet.  Both lead to an
  *     absorbing, non-accepting dead state.

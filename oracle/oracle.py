@@ -17,7 +17,7 @@ Contents
                          to check that every chunking composes to the sequential result.
 
 All arithmetic is on integers and exact; there is no tolerance anywhere.
-Conventions (readings of the paper, listed in the design doc):
+Conventions (readings of the paper):
   NONE (0xFFFFFFFF) in a table entry = undefined transition; a byte that maps to NONE16
   (0xFFFF) is outside the alphabet.  Both lead to the absorbing, non-accepting dead state,
   reported as NONE.  A match is counted after each symbol whose transition lands in F, at

@@ -10,7 +10,7 @@
  * of the sequential REM": start in q0 and take n steps).  There is no chunking and no
  * speculation here; the parallel method of Algorithm 1 must reproduce exactly this result.
  *
- * Readings of the paper that this file fixes (each listed in the design doc):
+ * Readings of the paper that this file fixes:
  *   - Undefined transitions (Algorithm 1 tests "Tt[q][c] in Q", i.e. an entry may be
  *     missing) and bytes outside the alphabet lead to an implicit absorbing, non-accepting
  *     dead state.  The dead state is reported as ORACLE_NONE.

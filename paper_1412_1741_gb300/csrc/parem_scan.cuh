@@ -584,14 +584,12 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
               while (bits) {
                 // up to four independent lookups in flight
                 uint32_t qs[4], nq[4];
-                int nb = 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                   qs[u] = kEmpty;
                   if (bits) {
                     qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
                     bits &= bits - 1;
-                    ++nb;
                   }
                 }
 #pragma unroll
@@ -599,7 +597,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                   if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
-                (void)nb;
               }
             }
             __syncwarp();

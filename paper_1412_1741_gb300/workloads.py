@@ -13,7 +13,7 @@ Texts
   uniform_text        -- i.i.d. uniform symbols.
   zipf_words_text     -- space-separated Zipf-distributed words with planted keywords.
 Workload recipes (the configurations that the tests and the benchmark use) are the
-``*_workload`` functions at the end; their sizes and seeds are stated in the design doc.
+``*_workload`` functions at the end, with their sizes and seeds.
 """
 from __future__ import annotations
 
