@@ -380,6 +380,9 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   pl->P = m_need <= 32 ? 1 : m_need <= 64 ? 2 : m_need <= 128 ? 4 : 8;
   pl->cand_stride = std::max<uint32_t>(1, std::max(P.max_cand, pl->enum_all ? P.n : 0u));
   pl->serial = serial_rows(dfa, m_need) ? 1u : 0u;
+  // fewer than one match per KiB in the last large scan: matches are rare enough that
+  // replaying the few vectors that hold one is cheaper than counting at every byte
+  pl->sparse = dfa->density_hint.load() < 1024u ? 1u : 0u;
   // lanes per row in the grouped speculation (P == 1): the smallest power of two that holds
   // the largest candidate set
   pl->group = 1;
@@ -502,6 +505,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.cand_stride = pl.cand_stride;
   p.serial_fallback = pl.serial;
   p.pos_base = pos_base;
+  p.sparse_count = pl.sparse;
   p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
   p.skip_publish = (o && o->debug_skip_publish_chunk > 0) ? o->debug_skip_publish_chunk : -1;
   if (!o) p.skip_publish = -1;
@@ -565,6 +569,9 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   sc->stats.cycles_bitmap = r.cyc_bitmap;
   sc->stats.cycles_lane = r.cyc_lane;
   if (pl.R) learn_convergence(dfa, pl.spec_cap, r.nonconv_rows, r.conv_max);
+  if (len >= (1u << 20) && !r.error)
+    const_cast<parem_dfa*>(dfa)->density_hint.store(
+        (uint32_t)std::min<uint64_t>(r.count / std::max<uint64_t>(1, len >> 20), 0xFFFFFFFEull));
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
   const uint32_t fs = r.final_state;

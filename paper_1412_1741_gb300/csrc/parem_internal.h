@@ -154,6 +154,9 @@ struct ScanParams {
   uint32_t serial_fallback;  // rows that did not merge are run from their resolved start
                              // (no slot maps); else every candidate gets a slot-map entry
   uint64_t pos_base;       // added to every position written (text offset of a piece)
+  uint32_t sparse_count;   // main run: track the largest state of each 16-byte vector and
+                           // count (by a replay of the vector) only where it is accepting
+  uint32_t pad2;
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch

@@ -23,6 +23,9 @@ struct parem_dfa {
   // longest speculative prefix (bytes) the candidates of this DFA needed so far, learned from
   // earlier scans; plans make rows several times longer than this
   std::atomic<uint32_t> conv_hint{0};
+  // matches per MiB of text in the last scan of at least 1 MiB (kEmpty: none yet); scans
+  // of DFAs that matched rarely count matches only in the 16-byte vectors that have one
+  std::atomic<uint32_t> density_hint{0xFFFFFFFFu};
 };
 
 namespace parem {
@@ -55,6 +58,7 @@ struct Plan {
   uint64_t h, S, R, tail, n_chunks;
   uint32_t spec_cap;
   uint32_t serial;       // unmerged rows run from their resolved start (no slot maps)
+  uint32_t sparse;       // count matches per 16-byte vector only where one occurs
 };
 
 // The launch plan of one scan (parem_api.cu).

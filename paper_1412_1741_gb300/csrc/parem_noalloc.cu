@@ -122,6 +122,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   p.spec_cap = pl.spec_cap;
   p.cand_stride = pl.cand_stride;
   p.serial_fallback = pl.serial;
+  p.sparse_count = pl.sparse;
   p.wait_budget = 4000000000ull;
   p.skip_publish = -1;
   p.ticket = reinterpret_cast<uint32_t*>(sb);

@@ -994,6 +994,23 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
               s = e & 31u;
               mu += e >> 5;
             }
+          } else if (p.sparse_count) {
+            // the largest state of the 16 steps says whether any was accepting (accepting
+            // states are numbered last); only then is the vector replayed to count
+            uint32_t mx = 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              s = tab.next(s, tab.col(byte_of(v[i], q)));
+              mx = max(mx, s);
+            }
+            if (mx >= A) {
+              uint32_t x = s0;
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                x = tab.next(x, tab.col(byte_of(v[i], q)));
+                mu += (x >= A);
+              }
+            }
           } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {

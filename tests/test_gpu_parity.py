@@ -240,6 +240,29 @@ def test_computed_columns(torch, extra):
     check(torch, spec, rng.integers(0, 256, size=50_001).astype(np.uint8), opts=pm.MatchOpts(segment_bytes=256))
 
 
+def test_sparse_counting_after_a_sparse_scan(torch):
+    # the first scan of a DFA learns its match density; once it is below one match per KiB,
+    # scans count matches only in the 16-byte vectors whose largest state is accepting
+    # (with a replay of that vector).  Both modes must give the oracle's result.
+    kws = wl.random_keywords(24, 6, 12, seed=8)
+    sym = wl.letters_byte_map()
+    t, acc = wl.aho_corasick_dfa([[int(sym[b]) for b in kw] for kw in kws], 27)
+    spec = wl.DfaSpec(t, 0, acc, sym, "ac24-sparse", {"keywords": kws})
+    text = wl.zipf_words_text(6 << 20, seed_words=4, seed_plants=5, plant_rate=2e-4, keywords=kws)
+    want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
+    assert 0 < want.match_count < 1024 * 6
+    dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    _, view = device_text(torch, text, 3)
+    for _ in range(3):  # dense first, then sparse
+        pos = torch.full((want.match_count,), -1, dtype=torch.int64, device="cuda")
+        got = pm.parem_match(dfa, view, pos, length=text.size)
+        assert (got.final_state, got.match_count) == (want.final_state, want.match_count)
+        assert np.array_equal(pos.cpu().numpy().astype(np.uint64), want.positions)
+        cnt = pm.parem_match(dfa, view, length=text.size)  # count only
+        assert cnt.match_count == want.match_count
+    dfa.free()
+
+
 def test_host_buffers_in_pieces(torch):
     # 200 MiB: the host path copies and scans 64 MiB pieces, each from the state the previous
     # one ended in; positions of all pieces land in one buffer, in order, with a capacity
