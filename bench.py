@@ -389,7 +389,7 @@ def run_serve(args, rank, world, local_rank):
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "errors": int((resp["status"] != 0).sum())}
 
-    srv = pm.parem_server_create(dfas)
+    srv = pm.parem_server_create(dfas, pm.ServerOpts(arenas=args.arenas))
     for w in range(args.warmup):
         srv.replay(trace(20000, 0.2, 100 + w))
     k0 = srv.stats()["kernels"]
@@ -432,6 +432,7 @@ def run_serve(args, rank, world, local_rank):
                        "step": "one replay of the whole trace"},
             "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
             "serving": {"batched": main, "batches": st["batches"], "max_batch": st["max_batch"],
+                        "arenas": args.arenas,
                         "fifo_plain": dict(fsum, trace_seconds=args.fifo_seconds), "fifo_results_agree": agree,
                         "saturation_sweep": sweep, "max_sustained_gbs": best["gbs"]},
             "e2e": {"value": main["gbs"], "unit": "GB/s", "h2d_bytes_per_step": int(len(req)) * 56,
@@ -669,6 +670,7 @@ def main():
     ap.add_argument("--batch-texts", type=int, default=4096, help="texts of the batched configuration")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
     ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
+    ap.add_argument("--arenas", type=int, default=8, help="batches in flight in the serving configuration")
     ap.add_argument("--ncu-report", default="", help="summarise this --set full report into profiles/")
     ap.add_argument("--ncu-launches", default="", help="summarise this ncu --csv launch list into profiles/")
     ap.add_argument("--ncu-command", default="", help="the command that made the report (recorded)")

@@ -255,10 +255,12 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
   }
 
   // Computed columns: when every byte outside one window [lo, lo + w) of ASCII (w <= 64) and
-  // one extra byte xb shares a single class, the column of a byte is arithmetic (window byte
-  // -> 2 + b - lo, xb -> 1, any other byte -> 0), so the scan needs no column-map lookup per
-  // byte.  The table then has w + 2 columns (each window byte its own, even where classes
-  // repeat); it must fit shared memory.
+  // one extra byte xb shares a single class, the column of a byte is arithmetic, so the scan
+  // needs no column-map lookup per byte: column min(b - lo + 2, w + 2) (unsigned; window
+  // bytes 2.., every byte below or above the window w + 2, and the bytes lo - 2, lo - 1 land
+  // on columns 0, 1), except xb -> w + 3.  Columns 0, 1 and w + 2 hold the shared class.
+  // The table then has w + 4 columns (each window byte its own, even where classes repeat);
+  // it must fit shared memory.
   if (P.layout != kByteSmem && P.n_classes >= 2) {
     std::vector<uint32_t> freq(P.n_classes, 0);
     for (int b = 0; b < 256; ++b) freq[P.byte_class[b]]++;
@@ -285,20 +287,22 @@ int prepare_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
       w = B[B.size() - 2] - lo + 1;
       xb = B.back();
     }
-    const uint32_t rb_win = row_pitch((uint32_t)w + 2, P.esize);
+    const uint32_t rb_win = row_pitch((uint32_t)w + 4, P.esize);
     if (lo >= 0 && xb >= 0 && (uint64_t)n * rb_win <= smem_table_budget) {
       P.layout = kClassWin;
       P.rowbytes = rb_win;
       P.table_bytes = (uint32_t)(((uint64_t)n * rb_win + 15) & ~15ull);
       P.table.assign(P.table_bytes, 0);
       auto column_of = [&](int b) -> uint32_t {
+        if (b == xb) return (uint32_t)w + 3u;
         if (b >= lo && b < lo + w) return 2u + (uint32_t)(b - lo);
-        return b == xb ? 1u : 0u;
+        if (b == lo - 2 || b == lo - 1) return (uint32_t)(b - lo + 2);
+        return (uint32_t)w + 2u;
       };
-      std::vector<int> rep(w + 2, other_byte);
-      rep[1] = xb;
+      std::vector<int> rep(w + 4, other_byte);
+      rep[w + 3] = xb;
       for (int i = 0; i < w; ++i) rep[2 + i] = lo + i;
-      for (uint32_t c = 0; c < (uint32_t)w + 2; ++c)
+      for (uint32_t c = 0; c < (uint32_t)w + 4; ++c)
         for (uint32_t s = 0; s < n; ++s) put(s, c * P.esize, cols[P.byte_class[rep[c]]][s]);
       for (int b = 0; b < 256; ++b) P.colmap[b] = (uint16_t)(column_of(b) * P.esize);
       P.win = (uint32_t)lo | ((uint32_t)w << 8) | ((uint32_t)xb << 16);

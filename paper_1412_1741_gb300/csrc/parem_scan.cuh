@@ -155,20 +155,25 @@ struct Tab {
   const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
   uint32_t smem_tier;      // kBatchDyn: 1 when the table is staged in shared memory
-  uint32_t win_lo, win_w, win_xb;  // kClassWin: window [lo, lo + w) and the extra byte
+  // kClassWin, from the window [lo, lo + w) and the extra byte xb: 2 * (2 - lo) (mod 2^32),
+  // 2 * (w + 2) and 2 * (w + 3) (column byte offsets for 2-byte entries), and xb
+  uint32_t win_k, win_cap, win_xcol, win_xb;
 
   __device__ __forceinline__ void set_win(uint32_t win) {
-    win_lo = win & 0xFFu;
-    win_w = (win >> 8) & 0xFFu;
+    const uint32_t lo = win & 0xFFu, w = (win >> 8) & 0xFFu;
+    win_k = 4u - 2u * lo;
+    win_cap = 2u * (w + 2u);
+    win_xcol = 2u * (w + 3u);
     win_xb = win >> 16;
   }
   __device__ __forceinline__ uint32_t col(uint32_t b) const {
     if (kByte) return b * ESIZE;
     if (kWin) {
-      // a few integer operations instead of a column-map read from shared memory
-      const uint32_t d = b - win_lo;
-      const uint32_t c = d < win_w ? d + 2u : (uint32_t)(b == win_xb);
-      return c * ESIZE;
+      // a shift-add, a minimum and a select instead of a column-map read from shared memory:
+      // column min(b - lo + 2, w + 2) (unsigned), or w + 3 for the extra byte
+      uint32_t c2 = min(2u * b + win_k, win_cap);
+      c2 = b == win_xb ? win_xcol : c2;
+      return ESIZE == 2 ? c2 : c2 >> 1;
     }
     if (kWide) return *reinterpret_cast<const uint16_t*>(sm + 2 * b);
     return sm[b];
