@@ -670,7 +670,7 @@ def main():
     ap.add_argument("--batch-texts", type=int, default=4096, help="texts of the batched configuration")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
     ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
-    ap.add_argument("--arenas", type=int, default=8, help="batches in flight in the serving configuration")
+    ap.add_argument("--arenas", type=int, default=32, help="batches in flight in the serving configuration")
     ap.add_argument("--ncu-report", default="", help="summarise this --set full report into profiles/")
     ap.add_argument("--ncu-launches", default="", help="summarise this ncu --csv launch list into profiles/")
     ap.add_argument("--ncu-command", default="", help="the command that made the report (recorded)")

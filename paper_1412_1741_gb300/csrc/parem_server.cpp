@@ -12,9 +12,10 @@
 //   allocated once; a batch is planned into a free arena (memory admission: requests are
 //   taken in arrival order while the count, byte and arena limits hold; a plan that does not
 //   fit is halved and the rest goes back to the head of the queue).
-// * With two arenas the next batch is launched while the previous one runs: its thread blocks
-//   start as soon as blocks of the running batch retire, so new arrivals do not wait for the
-//   slowest request of the batch ahead of them.
+// * With several arenas the next batches are launched while earlier ones run: their thread
+//   blocks start as soon as blocks of the running batches retire, so new arrivals do not
+//   wait for the slowest request of a batch ahead of them (32 arenas by default: with 2, a
+//   long request held the GPU's throughput to a third of that).
 // * FIFO mode serves one request at a time with parem_match (the plain comparison).
 #include <cuda_runtime.h>
 
@@ -345,7 +346,7 @@ extern "C" int parem_server_create(parem_dfa* const* dfas, uint32_t n_dfas, cons
         return rc;
       }
     }
-    const uint32_t n_arenas = s->opts.arenas ? s->opts.arenas : 2;
+    const uint32_t n_arenas = s->opts.arenas ? s->opts.arenas : 32;
     const uint32_t max_items = s->opts.max_items ? s->opts.max_items : 4096;
     const uint64_t scratch = s->opts.arena_scratch_bytes ? s->opts.arena_scratch_bytes : (256ull << 20);
     // descriptors: per item its scan parameters and tensor map, per slot its record, the CTA

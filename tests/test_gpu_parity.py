@@ -263,6 +263,28 @@ def test_sparse_counting_after_a_sparse_scan(torch):
     dfa.free()
 
 
+@pytest.mark.parametrize("seg", [0, 4160, 8192])
+def test_dense_emission_from_checkpoints(torch, seg):
+    # once a DFA's last large scan found at least one match per 64 bytes, pass 1 records the
+    # state and the count every 2 KiB of each row and the emit pass works on those pieces in
+    # parallel (rows whose candidates merge late start their first piece at the merge point;
+    # the last row's tail belongs to its last piece)
+    spec = wl.dense_dfa()
+    rng = np.random.default_rng(seg)
+    text = rng.integers(0, 256, size=(6 << 20) + 4099).astype(np.uint8)
+    dfa = load(spec)
+    _, view = device_text(torch, text, 5)
+    o = pm.MatchOpts(segment_bytes=seg)
+    pm.parem_match_ex(dfa, view, None, o, length=text.size)  # learns the density
+    want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
+    assert want.match_count > (text.size >> 6)
+    for cap in (want.match_count, want.match_count // 3):
+        pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+        got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
+        assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, cap)
+        assert np.array_equal(pos.cpu().numpy().astype(np.uint64), want.positions[:cap])
+
+
 def test_host_buffers_in_pieces(torch):
     # 200 MiB: the host path copies and scans 64 MiB pieces, each from the state the previous
     # one ended in; positions of all pieces land in one buffer, in order, with a capacity
