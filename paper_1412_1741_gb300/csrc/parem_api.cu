@@ -347,7 +347,9 @@ uint64_t max_row_bytes(const parem_dfa* dfa, uint32_t m) {
 
 uint64_t min_row_bytes(const parem_dfa* dfa, uint32_t P) {
   const Prepared& H = dfa->host;
-  uint64_t smin = P == 1 ? 512 : 4096;
+  // grouped speculation of small candidate sets costs little per row: short rows keep small
+  // texts spread over many warps
+  uint64_t smin = P == 1 ? 128 : 4096;
   // rows several times longer than the candidates need to merge: the estimate from random
   // input (prepare time) or the longest merge seen on real input, whichever is larger
   const uint64_t est = H.sync_len == kNoSync ? 0 : H.sync_len;
@@ -479,14 +481,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
-  // dense matches (the last large scan of this DFA found at least one per 64 bytes): the emit
-  // pass works on 2 KiB pieces of each row from checkpoints pass 1 records
-  const uint32_t cpr = (emit && pl.R && dfa->density_hint.load() != 0xFFFFFFFFu &&
-                        dfa->density_hint.load() >= 16384u)
-                           ? (uint32_t)((pl.S + kCkptBytes - 1) / kCkptBytes)
-                           : 0u;
-  const uint64_t o_ckpt = round_up(o_slot + 2 * slot_bytes, 256);
-  const uint64_t total = round_up(o_ckpt + pl.R * (uint64_t)cpr * 8, 256);
+  const uint64_t total = round_up(o_slot + 2 * slot_bytes, 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
   uint8_t* sb = static_cast<uint8_t*>(sc->dev);
@@ -513,8 +508,6 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.serial_fallback = pl.serial;
   p.pos_base = pos_base;
   p.sparse_count = pl.sparse;
-  p.ckpt_per_row = cpr;
-  p.ckpt = cpr ? reinterpret_cast<uint2*>(sb + o_ckpt) : nullptr;
   p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
   p.skip_publish = (o && o->debug_skip_publish_chunk > 0) ? o->debug_skip_publish_chunk : -1;
   if (!o) p.skip_publish = -1;

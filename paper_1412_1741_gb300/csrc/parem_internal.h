@@ -22,7 +22,6 @@ constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4 + 48;
 constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
 constexpr uint32_t kSlotsFlag = 2u;      // SegRec.flags: every main-run match of the row is in its slots
 constexpr uint32_t kPreFlag = 4u;        // SegRec.flags: replay the merged prefix [0, t) from x
-constexpr uint32_t kCkptFlag = 8u;       // SegRec.flags: main-run matches via the row's checkpoints
 constexpr uint32_t kRowSlots = 16;       // match positions pass 1 records per row
 constexpr uint64_t kMaxText = 1ull << 45;
 
@@ -114,10 +113,6 @@ struct SegRec {
   uint32_t pre;     // matches in the head and the merged prefix
 };
 
-// Dense emission: the emit pass works on pieces of this many bytes of a row in parallel,
-// each from a state pass 1 recorded at the piece's start.
-constexpr uint32_t kCkptBytes = 2048;
-
 // Scratch bytes per row for recorded match positions (row-relative u32).
 constexpr uint32_t kRowSlotBytes = kRowSlots * 4;
 
@@ -161,10 +156,7 @@ struct ScanParams {
   uint64_t pos_base;       // added to every position written (text offset of a piece)
   uint32_t sparse_count;   // main run: track the largest state of each 16-byte vector and
                            // count (by a replay of the vector) only where it is accepting
-  uint32_t ckpt_per_row;   // dense emission: checkpoints per row (0: none), one per kCkptBytes
-  uint2* ckpt;             // [R][ckpt_per_row]: {state, main-run matches before} at the
-                           // checkpoint (or at the merge point t for the first one after it);
-                           // state kEmpty for checkpoints inside the speculated prefix
+  uint32_t pad2;
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch

@@ -952,12 +952,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
   const bool run = active && my_conv;
   uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
-  if (p.ckpt_per_row && run) {
-    // checkpoints inside the speculated prefix have no main-run state
-    // (the one holding the merge point t is written again below, with the state at t)
-    for (uint32_t k = 0; k * kCkptBytes < my_t && k < p.ckpt_per_row; ++k)
-      p.ckpt[myrow * p.ckpt_per_row + k] = make_uint2(kEmpty, 0u);
-  }
   for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
     const uint32_t b = blk % kStages;
     const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
@@ -990,9 +984,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         const uint32_t col = col0 + i * 16u;
         if (col >= my_t) {
           const uint32_t mu0 = mu, s0 = s;
-          // dense emission: the state and the count at each checkpoint (and at the merge point)
-          if (p.ckpt_per_row && (col % kCkptBytes == 0 || col == my_t))
-            p.ckpt[myrow * p.ckpt_per_row + col / kCkptBytes] = make_uint2(s, mu);
           if constexpr (LAYOUT == kByteStride) {
             // four bytes per lookup: the stride table holds the state after them and how
             // many of the four steps end in an accepting state
@@ -1337,8 +1328,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         sr.ls = ls;
         // every main-run match was recorded by pass 1: the emit pass only copies them
         if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
-        else if (main_live && p.ckpt_per_row && my_t < p.S) sr.flags |= kCkptFlag;
-        sr.t = my_t;  // the merge point (the first checkpoint's start when kCkptFlag)
       }
       p.segrec[myrow] = sr;
     }
@@ -1529,66 +1518,6 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
     emit_row<LAYOUT, ESIZE>(tab, p, r);
 }
 
-// Dense emission: one thread per (row, checkpoint piece).  Rows pass 1 flagged kCkptFlag
-// replay each piece [max(k * kCkptBytes, t), next checkpoint) from the state recorded at its
-// start and write its matches at the row's offset + the prefix's matches + the main-run
-// matches before the piece; the thread of piece 0 also writes the head or prefix matches.
-// Other rows are emitted whole by the thread of piece 0.
-template <int LAYOUT, int ESIZE>
-__global__ void __launch_bounds__(1024) k_emit_dense(const ScanParams p) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  uint8_t* const sm = smem_raw;
-  const DeviceDfa& D = p.dfa;
-  load_tables<LAYOUT, ESIZE>(sm, D);
-  __syncthreads();
-  Tab<LAYOUT, ESIZE> tab;
-  tab.sm = sm;
-  tab.gtable = D.table;
-  tab.rowbytes = D.rowbytes;
-  tab.smem_tier = 1;
-  tab.set_win(p.dfa.win);
-  const uint32_t A = D.first_accept;
-  const uint64_t cpr = p.ckpt_per_row;
-  const uint64_t items = p.R * cpr;
-  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
-       it += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t r = it / cpr, k = it % cpr;
-    const SegRec sr = p.segrec[r];
-    if (sr.count == 0 || sr.offset >= p.capacity) continue;
-    if (!(sr.flags & kCkptFlag)) {
-      if (k == 0) emit_row<LAYOUT, ESIZE>(tab, p, r);
-      continue;
-    }
-    if (k == 0 && (sr.flags & (kHeadFlag | kPreFlag))) {
-      const uint64_t end = (sr.offset + sr.pre < p.capacity) ? sr.offset + sr.pre : p.capacity;
-      uint64_t o = sr.offset;
-      uint32_t x = sr.x;
-      if (sr.flags & kHeadFlag) {
-        for (uint64_t i = 0; i < p.h && o < end; ++i) {
-          x = tab.next(x, tab.col(ldg8(p.text + i)));
-          if (x >= A) p.positions[o++] = p.pos_base + i;
-        }
-      } else {
-        emit_range(tab, p, r, 0u, sr.t, x, o, end);
-      }
-    }
-    const uint2 c = p.ckpt[r * cpr + k];
-    if (c.x == kEmpty) continue;  // inside the speculated prefix
-    const uint32_t main_total = sr.count - sr.pre;
-    const uint32_t mu_next = k + 1 < cpr ? p.ckpt[r * cpr + k + 1].y : main_total;
-    if (mu_next == c.y) continue;
-    const uint32_t from = (uint32_t)k * kCkptBytes > sr.t ? (uint32_t)k * kCkptBytes : sr.t;
-    const bool last = r == p.R - 1;
-    const uint32_t to = k + 1 < cpr ? (uint32_t)(k + 1) * kCkptBytes : (uint32_t)(p.S + (last ? p.tail : 0));
-    uint64_t o = sr.offset + sr.pre + c.y;
-    const uint64_t end0 = sr.offset + sr.pre + mu_next;
-    const uint64_t end = end0 < p.capacity ? end0 : p.capacity;
-    if (o >= end) continue;
-    uint32_t x = c.x;
-    emit_range(tab, p, r, from, to, x, o, end);
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 // Texts too short for one row: a single thread runs the plain loop on the device.
 // ---------------------------------------------------------------------------------------
@@ -1763,7 +1692,7 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t stream) {
-  auto kern = p.ckpt_per_row ? k_emit_dense<LAYOUT, ESIZE> : k_emit<LAYOUT, ESIZE>;
+  auto kern = k_emit<LAYOUT, ESIZE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // One thread per row: the block size that keeps the most threads resident (the table in
@@ -1779,7 +1708,10 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
       best_blocks = nb;
     }
   }
-  kern<<<grid * best_blocks, best_block, smem, stream>>>(p);
+  // no more blocks than there are rows to cover: every block stages the table
+  const uint64_t need = (p.R + best_block - 1) / best_block;
+  const int blocks = (int)std::min<uint64_t>((uint64_t)grid * best_blocks, std::max<uint64_t>(need, 1));
+  kern<<<blocks, best_block, smem, stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -264,20 +264,27 @@ def test_sparse_counting_after_a_sparse_scan(torch):
 
 
 @pytest.mark.parametrize("seg", [0, 4160, 8192])
-def test_dense_emission_from_checkpoints(torch, seg):
-    # once a DFA's last large scan found at least one match per 64 bytes, pass 1 records the
-    # state and the count every 2 KiB of each row and the emit pass works on those pieces in
-    # parallel (rows whose candidates merge late start their first piece at the merge point;
-    # the last row's tail belongs to its last piece)
+def test_dense_emission(torch, seg):
+    # dense matches (10 %, then a stretch where every byte matches): every row replays its
+    # whole window; positions in order, with and without capacity truncation
     spec = wl.dense_dfa()
     rng = np.random.default_rng(seg)
     text = rng.integers(0, 256, size=(6 << 20) + 4099).astype(np.uint8)
+    # in the last 1 MiB the automaton accepts after every byte (ten times the density)
+    t = np.asarray(spec.table)
+    acc = np.asarray(spec.accept).astype(bool)
+    q = int(oracle.scan(spec.table, None, spec.start, spec.accept, text[: -(1 << 20)]).final_state)
+    first_acc = np.argmax(acc[t], axis=1)  # per state, the first byte that leads to F
+    tail = np.empty(1 << 20, np.uint8)
+    for j in range(tail.size):
+        tail[j] = first_acc[q]
+        q = int(t[q, tail[j]])
+    text[-(1 << 20):] = tail
     dfa = load(spec)
     _, view = device_text(torch, text, 5)
     o = pm.MatchOpts(segment_bytes=seg)
-    pm.parem_match_ex(dfa, view, None, o, length=text.size)  # learns the density
     want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
-    assert want.match_count > (text.size >> 6)
+    assert want.match_count > (text.size >> 6) + (1 << 20)
     for cap in (want.match_count, want.match_count // 3):
         pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
         got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
