@@ -417,9 +417,26 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   } else {
     const uint64_t smax = max_row_bytes(dfa, m_need);
     const uint64_t smin = std::min(min_row_bytes(dfa, pl->P), smax);
-    S = round_up(std::max<uint64_t>(body / (lanes_total * 2 + 1), 1), kBox);
-    S = std::max(S, smin);
-    S = std::min<uint64_t>(S, std::max<uint64_t>(smin, std::min<uint64_t>(smax, 1u << 20)));
+    const uint64_t shi = std::max<uint64_t>(smin, std::min<uint64_t>(smax, 1u << 20));
+    // One wave: rows long enough that every warp owns at most one chunk.  All chunks then
+    // run at once and finish together, so no look-back waits on a predecessor that started
+    // later, and the per-chunk work (speculation, pipeline fill) is paid once per warp.
+    S = round_up(std::max<uint64_t>((body + lanes_total - 1) / lanes_total, 1), kBox);
+    S = std::min<uint64_t>(std::max(S, smin), shi);
+    // The tail (body mod S) is run by the last row's lane after its row, which puts it on
+    // the critical path: among the next 64 row lengths (still one wave) take the one with
+    // the least S + tail.
+    if (body >= S) {
+      uint64_t best = S, best_cost = S + body % S;
+      for (uint64_t c = S + kBox; c <= std::min<uint64_t>(S + 64 * kBox, shi); c += kBox) {
+        const uint64_t cost = c + body % c;
+        if (cost < best_cost) {
+          best = c;
+          best_cost = cost;
+        }
+      }
+      S = best;
+    }
   }
   // keep the row index inside the TMA coordinate range
   while (body / S >= (1ull << 31)) S *= 2;
