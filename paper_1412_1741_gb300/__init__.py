@@ -265,6 +265,9 @@ def _ptr_len(buf, length=None):
 def _stream(stream):
     if stream is None:
         import torch
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        if raw is not None:  # the current stream's handle without building a Stream object
+            return ctypes.c_void_p(raw(torch._C._cuda_getDevice()))
         return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     if hasattr(stream, "cuda_stream"):
         return ctypes.c_void_p(stream.cuda_stream)

@@ -37,6 +37,14 @@ constexpr uint32_t kSmemTableBudget = 160 * 1024;
 struct Scratch {
   void* dev = nullptr;
   size_t bytes = 0;
+  // Two header regions [ticket 256 B][result 256 B][status words], hdr_bytes each.  A scan
+  // uses region cur, which is all zero, and its first kernel zeroes the other region (the
+  // previous scan's), so no memset precedes the launches.  used[i]: bytes of region i that
+  // its last scan may have written (0: clean).
+  void* hdr = nullptr;
+  size_t hdr_bytes = 0;
+  uint32_t cur = 0;
+  size_t used[2] = {0, 0};
   DevResult* host_res = nullptr;  // pinned
   void* dev_text = nullptr;       // staging for parem_match_host
   size_t text_bytes = 0;
@@ -309,6 +317,7 @@ extern "C" int parem_release_scratch(void* stream) {
   }
   cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (s->dev) cudaFree(s->dev);
+  if (s->hdr) cudaFree(s->hdr);
   if (s->dev_text) cudaFree(s->dev_text);
   if (s->dev_pos) cudaFree(s->dev_pos);
   if (s->host_res) cudaFreeHost(s->host_res);
@@ -491,18 +500,41 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   if (!sc->host_res) {
     if (cudaMallocHost(&sc->host_res, sizeof(DevResult)) != cudaSuccess) return PAREM_ERR_OOM;
   }
-  // scratch: [ticket 256][result 256][status K*8][segrec R*16][slot_end][slot_cnt]
-  const bool emit = positions != nullptr && capacity > 0;
+  // header (double-buffered, see Scratch): [ticket 256][result 256][status K*8]
   const uint64_t o_status = 512;
-  const uint64_t o_segrec = round_up(o_status + pl.n_chunks * 8, 256);
+  const uint64_t hdr_need = round_up(o_status + pl.n_chunks * 8, 256);
+  if (!sc->hdr || sc->hdr_bytes < hdr_need) {
+    if (sc->hdr) cudaFree(sc->hdr);
+    sc->hdr = nullptr;
+    sc->hdr_bytes = 0;
+    const size_t sz = round_up(std::max<uint64_t>(hdr_need, sc->hdr_bytes * 3 / 2), 4096);
+    cudaError_t ae = cudaMalloc(&sc->hdr, 2 * sz);
+    if (ae != cudaSuccess) {
+      sc->hdr = nullptr;
+      return ae == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
+    }
+    sc->hdr_bytes = sz;
+    sc->cur = 0;
+    sc->used[0] = sc->used[1] = 0;
+    PAREM_CUDA_TRY(cudaMemsetAsync(sc->hdr, 0, 2 * sz, stream));
+  }
+  if (sc->used[sc->cur]) {  // an earlier scan stopped before its kernel cleared this region
+    PAREM_CUDA_TRY(cudaMemsetAsync(static_cast<uint8_t*>(sc->hdr) + sc->cur * sc->hdr_bytes, 0,
+                                   sc->used[sc->cur], stream));
+    sc->used[sc->cur] = 0;
+  }
+  uint8_t* hb = static_cast<uint8_t*>(sc->hdr) + sc->cur * sc->hdr_bytes;
+  uint8_t* hb_other = static_cast<uint8_t*>(sc->hdr) + (sc->cur ^ 1u) * sc->hdr_bytes;
+  // scratch: [segrec R*16][row slots][slot_end][slot_cnt]
+  const bool emit = positions != nullptr && capacity > 0;
+  const uint64_t o_segrec = 0;
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
-  const uint64_t total = round_up(o_slot + 2 * slot_bytes, 256);
+  const uint64_t total = round_up(std::max<uint64_t>(o_slot + 2 * slot_bytes, 256), 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
   uint8_t* sb = static_cast<uint8_t*>(sc->dev);
-  PAREM_CUDA_TRY(cudaMemsetAsync(sb, 0, o_status + pl.n_chunks * 8, stream));
 
   ScanParams p;
   std::memset(&p, 0, sizeof(p));
@@ -528,9 +560,11 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.wait_budget = o && o->wait_budget_cycles ? o->wait_budget_cycles : 4000000000ull;
   p.skip_publish = (o && o->debug_skip_publish_chunk > 0) ? o->debug_skip_publish_chunk : -1;
   if (!o) p.skip_publish = -1;
-  p.ticket = reinterpret_cast<uint32_t*>(sb);
-  p.result = reinterpret_cast<DevResult*>(sb + 256);
-  p.status = reinterpret_cast<unsigned long long*>(sb + o_status);
+  p.ticket = reinterpret_cast<uint32_t*>(hb);
+  p.result = reinterpret_cast<DevResult*>(hb + 256);
+  p.status = reinterpret_cast<unsigned long long*>(hb + o_status);
+  p.clear = reinterpret_cast<uint4*>(hb_other);
+  p.clear_n16 = round_up(sc->used[sc->cur ^ 1u], 16) / 16;
   p.segrec = emit ? reinterpret_cast<SegRec*>(sb + o_segrec) : nullptr;
   p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
@@ -574,7 +608,11 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   }
   if (e == cudaSuccess && timed && pl.R == 0) e = cudaEventRecord(sc->ev[1], stream);
   if (e == cudaSuccess && timed) e = cudaEventRecord(sc->ev[2], stream);
+  // region cur is written from here on; the kernel (if it launched) cleared the other one
+  sc->used[sc->cur] = hdr_need;
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
+  sc->used[sc->cur ^ 1u] = 0;
+  sc->cur ^= 1u;
   PAREM_CUDA_TRY(cudaMemcpyAsync(sc->host_res, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, stream));
   PAREM_CUDA_TRY(cudaStreamSynchronize(stream));
   const DevResult r = *sc->host_res;

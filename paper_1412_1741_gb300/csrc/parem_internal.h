@@ -167,6 +167,8 @@ struct ScanParams {
   uint32_t* slot_end;      // R * cand_stride
   uint32_t* slot_cnt;      // R * cand_stride
   DevResult* result;
+  uint4* clear;            // zeroed by the kernel (clear_n16 16-byte words): the header
+  uint64_t clear_n16;      // region of the previous scan, which the next scan reuses
   // outputs
   uint64_t* positions;
   uint64_t capacity;

@@ -37,6 +37,7 @@
 #define PAREM_CONV_STATS 1
 #endif
 
+#include <atomic>
 #include <cstdint>
 
 #include "parem_internal.h"
@@ -1363,12 +1364,21 @@ __device__ __forceinline__ void drain_stages(const WarpCtx& wc, uint64_t budget)
 // Pass 1: speculation, main run, look-back.  P = candidate registers per lane when one row
 // is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
 // ---------------------------------------------------------------------------------------
+// Zero the previous scan's header region (its ticket, result and status words), which the
+// next scan on the stream reuses; every thread of the grid takes a strided share.
+__device__ __forceinline__ void clear_prev_header(const ScanParams& p) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.clear_n16; i += stride)
+    p.clear[i] = make_uint4(0, 0, 0, 0);
+}
+
 template <int LAYOUT, int ESIZE, int P>
 __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
     k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  clear_prev_header(p);
   load_tables<LAYOUT, ESIZE>(sm, p.dfa);
   const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
   WarpCtx wc;
@@ -1526,6 +1536,7 @@ __global__ void k_tiny(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
   const DeviceDfa& D = p.dfa;
+  clear_prev_header(p);
   load_tables<LAYOUT, ESIZE>(sm, D);
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -1680,11 +1691,29 @@ __global__ void k_batch_tiny(const __grid_constant__ BatchParams bp, const uint3
 #endif  // PAREM_BATCH_KERNELS
 
 // Launch wrappers, instantiated in the per-layout translation units.
+//
+// The dynamic shared memory limit of a kernel is raised once per device to the largest size
+// launched so far (one slot per device ordinal below 64; others set it at every launch).
+template <typename K>
+cudaError_t raise_smem_limit(K kern, size_t smem, std::atomic<size_t>* limits) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  if (dev >= 0 && dev < 64 && limits[dev].load(std::memory_order_relaxed) >= smem) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) {
+    size_t cur = limits[dev].load(std::memory_order_relaxed);
+    while (cur < smem && !limits[dev].compare_exchange_weak(cur, smem)) {
+    }
+  }
+  return e;
+}
+
 template <int LAYOUT, int ESIZE, int P>
 cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int grid, int block,
                              size_t smem, cudaStream_t stream) {
+  static std::atomic<size_t> limits[64];
   auto kern = k_spec_scan<LAYOUT, ESIZE, P>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(kern, smem, limits);
   if (e != cudaSuccess) return e;
   kern<<<grid, block, smem, stream>>>(tmap, p);
   return cudaGetLastError();
@@ -1692,21 +1721,35 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t stream) {
+  static std::atomic<size_t> limits[64];
+  // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
+  static std::atomic<uint64_t> choice[64];
   auto kern = k_emit<LAYOUT, ESIZE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(kern, smem, limits);
   if (e != cudaSuccess) return e;
   // One thread per row: the block size that keeps the most threads resident (the table in
   // shared memory is per block, so larger blocks share it among more rows), one wave of
   // resident blocks.  `grid` carries the SM count and `block` the smallest block size.
+  int dev = 0;
+  cudaGetDevice(&dev);
   int best_threads = 0, best_block = block, best_blocks = 1;
-  for (int b = block; b <= 1024; b *= 2) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, b, smem) != cudaSuccess) continue;
-    if (nb * b > best_threads) {
-      best_threads = nb * b;
-      best_block = b;
-      best_blocks = nb;
+  const uint64_t c = (dev >= 0 && dev < 64) ? choice[dev].load(std::memory_order_relaxed) : 0;
+  if (c && (c >> 24) == smem) {
+    best_blocks = (int)((c >> 12) & 0xFFF);
+    best_block = (int)(c & 0xFFF);
+  } else {
+    for (int b = block; b <= 1024; b *= 2) {
+      int nb = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, b, smem) != cudaSuccess) continue;
+      if (nb * b > best_threads) {
+        best_threads = nb * b;
+        best_block = b;
+        best_blocks = nb;
+      }
     }
+    if (dev >= 0 && dev < 64 && best_blocks < 4096)
+      choice[dev].store((uint64_t)smem << 24 | (uint64_t)best_blocks << 12 | (uint64_t)best_block,
+                        std::memory_order_relaxed);
   }
   // no more blocks than there are rows to cover: every block stages the table
   const uint64_t need = (p.R + best_block - 1) / best_block;
@@ -1717,8 +1760,9 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
 
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_tiny(const ScanParams& p, size_t smem, cudaStream_t stream) {
+  static std::atomic<size_t> limits[64];
   auto kern = k_tiny<LAYOUT, ESIZE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(kern, smem, limits);
   if (e != cudaSuccess) return e;
   kern<<<1, 128, smem, stream>>>(p);
   return cudaGetLastError();
