@@ -540,15 +540,21 @@ def run_ours(args, rank, world, local_rank):
         host_text.copy_(text)
         host_pos = torch.empty(max(cap, 1), dtype=torch.int64, pin_memory=True) if cap else None
         pm.parem_match_host(dfa, host_text, host_pos)
-        e2e_steps = max(2, min(args.steps, 5))
+        e2e_steps = max(3, min(args.steps, 7))
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        step_s = []
         for _ in range(e2e_steps):
+            t0 = time.perf_counter()
             re2e = pm.parem_match_host(dfa, host_text, host_pos)
-        dt = time.perf_counter() - t0
+            step_s.append(time.perf_counter() - t0)
+        step_s.sort()
         if rank == 0:
-            line["e2e"] = {"value": round(n * e2e_steps / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": n,
-                           "d2h_bytes_per_step": re2e.n_written * 8 + 24, "steps": e2e_steps}
+            # median step: single steps of the host copy path now and then run at a fraction
+            # of the link rate on these hosts, in both the current and earlier builds
+            line["e2e"] = {"value": round(n / step_s[len(step_s) // 2] / 1e9, 2), "unit": "GB/s",
+                           "h2d_bytes_per_step": n, "d2h_bytes_per_step": re2e.n_written * 8 + 24,
+                           "steps": e2e_steps, "statistic": "median step",
+                           "mean_value": round(n * e2e_steps / sum(step_s) / 1e9, 2)}
         del host_text, host_pos
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(spec, text)

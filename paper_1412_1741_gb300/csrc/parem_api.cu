@@ -393,7 +393,11 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   pl->serial = serial_rows(dfa, m_need) ? 1u : 0u;
   // fewer than one match per KiB in the last large scan: matches are rare enough that
   // replaying the few vectors that hold one is cheaper than counting at every byte
-  pl->sparse = dfa->density_hint.load() < 1024u ? 1u : 0u;
+  const uint32_t density = dfa->density_hint.load();
+  pl->sparse = density < 1024u ? 1u : 0u;
+  // at least one match per 64 bytes: a row's replay in the emit pass is long serial work,
+  // so it is split into pieces that run in parallel
+  pl->dense = (density != 0xFFFFFFFFu && density >= 16384u) ? 1u : 0u;
   // lanes per row in the grouped speculation (P == 1): the smallest power of two that holds
   // the largest candidate set
   pl->group = 1;
@@ -531,7 +535,9 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
-  const uint64_t total = round_up(std::max<uint64_t>(o_slot + 2 * slot_bytes, 256), 256);
+  const uint32_t cpr = (emit && pl.dense && pl.R) ? (uint32_t)((pl.S + kCkptBytes - 1) / kCkptBytes) : 0u;
+  const uint64_t o_ckpt = round_up(o_slot + 2 * slot_bytes, 256);
+  const uint64_t total = round_up(std::max<uint64_t>(o_ckpt + pl.R * (uint64_t)cpr * 8, 256), 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
   uint8_t* sb = static_cast<uint8_t*>(sc->dev);
@@ -569,6 +575,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
+  p.ckpt_per_row = cpr;
+  p.ckpt = cpr ? reinterpret_cast<uint2*>(sb + o_ckpt) : nullptr;
   p.positions = emit ? positions : nullptr;
   p.capacity = emit ? capacity : 0;
 

@@ -59,6 +59,8 @@ struct Plan {
   uint32_t spec_cap;
   uint32_t serial;       // unmerged rows run from their resolved start (no slot maps)
   uint32_t sparse;       // count matches per 16-byte vector only where one occurs
+  uint32_t dense;        // matches were dense in the DFA's last large scan: emit positions in
+                         // pieces from checkpoints pass 1 writes
 };
 
 // The launch plan of one scan (parem_api.cu).

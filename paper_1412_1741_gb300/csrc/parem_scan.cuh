@@ -953,6 +953,14 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
   const bool run = active && my_conv;
   uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
+  if (p.ckpt_per_row && run) {
+    // dense emission: pieces that end inside the merged prefix have no main-run state; the
+    // piece holding the merge point t starts there (state my_sigma, no matches before it)
+    const uint32_t kt = my_t / kCkptBytes;
+    for (uint32_t k = 0; k < kt && k < p.ckpt_per_row; ++k)
+      p.ckpt[myrow * p.ckpt_per_row + k] = make_uint2(kEmpty, 0u);
+    if (kt < p.ckpt_per_row) p.ckpt[myrow * p.ckpt_per_row + kt] = make_uint2(my_sigma, 0u);
+  }
   for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
     const uint32_t b = blk % kStages;
     const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
@@ -980,6 +988,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
     if (run) {
       const uint32_t col0 = blk * kBox;
+      // dense emission: the state and the count at each later piece start
+      if (p.ckpt_per_row && col0 % kCkptBytes == 0 && col0 > my_t)
+        p.ckpt[myrow * p.ckpt_per_row + col0 / kCkptBytes] = make_uint2(s, mu);
 #pragma unroll
       for (uint32_t i = 0; i < kBox / 16; ++i) {
         const uint32_t col = col0 + i * 16u;
@@ -991,14 +1002,32 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
             const uint32_t K = D.stride_k, km = K - 1, k4 = K * K * K * K;
             const uint8_t* stab = sm + kTableOff + D.stride_off;
             const uint32_t ws[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+            if (K <= 6) {
+              // the four symbols of a word at once: clamp every byte to K - 1 (bit 7 of
+              // (b | 0x80) - K is set when b & 0x7F >= K; bytes >= 128 clamp too), then the
+              // mixed-radix index m0 K^3 + m1 K^2 + m2 K + m3 as one byte dot product
+              const uint32_t ones = 0x01010101u, kmrep = km * ones;
+              const uint32_t wts = K * K * K | (K * K) << 8 | K << 16 | 1u << 24;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const uint32_t w = ws[g];
-              const uint32_t m0 = min(w & 0xFFu, km), m1 = min((w >> 8) & 0xFFu, km);
-              const uint32_t m2 = min((w >> 16) & 0xFFu, km), m3 = min(w >> 24, km);
-              const uint32_t e = stab[s * k4 + ((m0 * K + m1) * K + m2) * K + m3];
-              s = e & 31u;
-              mu += e >> 5;
+              for (int g = 0; g < 4; ++g) {
+                const uint32_t w = ws[g];
+                const uint32_t over = (((w | 0x80808080u) - K * ones) | w) & 0x80808080u;
+                const uint32_t mask = (over >> 7) * 0xFFu;
+                const uint32_t m = (w & ~mask) | (kmrep & mask);
+                const uint32_t e = stab[__dp4a(m, wts, s * k4)];
+                s = e & 31u;
+                mu += e >> 5;
+              }
+            } else {
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                const uint32_t w = ws[g];
+                const uint32_t m0 = min(w & 0xFFu, km), m1 = min((w >> 8) & 0xFFu, km);
+                const uint32_t m2 = min((w >> 16) & 0xFFu, km), m3 = min(w >> 24, km);
+                const uint32_t e = stab[s * k4 + ((m0 * K + m1) * K + m2) * K + m3];
+                s = e & 31u;
+                mu += e >> 5;
+              }
             }
           } else if (p.sparse_count) {
             // the largest state of the 16 steps says whether any was accepting (accepting
@@ -1329,6 +1358,10 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         sr.ls = ls;
         // every main-run match was recorded by pass 1: the emit pass only copies them
         if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
+        else if (main_live && p.ckpt_per_row && my_t < p.S) {
+          sr.flags |= kCkptFlag;
+          sr.t = my_t;  // the first piece starts at the merge point
+        }
       }
       p.segrec[myrow] = sr;
     }
@@ -1433,16 +1466,24 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
   const uint64_t gbase = p.h + r * p.S;
   const uint32_t A = p.dfa.first_accept;
   uint64_t off = from;
-  // aligned whole vectors inside the row, with the next vector's load in flight
+  // aligned whole vectors inside the row, with the next vector's load in flight: the steps
+  // of a vector collect a 16-bit mask of accepting positions, written after the vector
+  // (one store per match instead of a predicated store at every byte)
   if ((off & 15u) == 0 && off + 16 <= p.S && off + 16 <= to) {
     uint4 nxt = ldg16(rowp + off);
     while (off + 16 <= p.S && off + 16 <= to && o < end) {
       const uint4 v = nxt;
       if (off + 32 <= p.S && off + 32 <= to) nxt = ldg16(rowp + off + 16);
+      uint32_t m = 0;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         x = tab.next(x, tab.col(byte_of(v, i)));
-        if (x >= A && o < end) p.positions[o++] = p.pos_base + gbase + off + (uint64_t)i;
+        m |= (x >= A ? 1u : 0u) << i;
+      }
+      const uint64_t pb = p.pos_base + gbase + off;
+      while (m != 0 && o < end) {
+        p.positions[o++] = pb + (uint64_t)(__ffs(m) - 1);
+        m &= m - 1u;
       }
       off += 16;
     }
@@ -1526,6 +1567,66 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
        r += (uint64_t)gridDim.x * blockDim.x)
     emit_row<LAYOUT, ESIZE>(tab, p, r);
+}
+
+// Dense emission: one thread per (row, piece of kCkptBytes).  Rows pass 1 flagged kCkptFlag
+// replay each piece [max(k kCkptBytes, t), next piece) from the state recorded at its start
+// and write its matches at the row's offset + the prefix's matches + the main-run matches
+// before the piece; the thread of piece 0 also writes the head or prefix matches.  Other
+// rows are emitted whole by the thread of piece 0.
+template <int LAYOUT, int ESIZE>
+__global__ void __launch_bounds__(1024) k_emit_dense(const ScanParams p) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const DeviceDfa& D = p.dfa;
+  load_tables<LAYOUT, ESIZE>(sm, D);
+  __syncthreads();
+  Tab<LAYOUT, ESIZE> tab;
+  tab.sm = sm;
+  tab.gtable = D.table;
+  tab.rowbytes = D.rowbytes;
+  tab.smem_tier = 1;
+  tab.set_win(p.dfa.win);
+  const uint32_t A = D.first_accept;
+  const uint64_t cpr = p.ckpt_per_row;
+  const uint64_t items = p.R * cpr;
+  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
+       it += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = it / cpr, k = it % cpr;
+    const SegRec sr = p.segrec[r];
+    if (sr.count == 0 || sr.offset >= p.capacity) continue;
+    if (!(sr.flags & kCkptFlag)) {
+      if (k == 0) emit_row<LAYOUT, ESIZE>(tab, p, r);
+      continue;
+    }
+    if (k == 0 && (sr.flags & (kHeadFlag | kPreFlag))) {
+      const uint64_t end = (sr.offset + sr.pre < p.capacity) ? sr.offset + sr.pre : p.capacity;
+      uint64_t o = sr.offset;
+      uint32_t x = sr.x;
+      if (sr.flags & kHeadFlag) {
+        for (uint64_t i = 0; i < p.h && o < end; ++i) {
+          x = tab.next(x, tab.col(ldg8(p.text + i)));
+          if (x >= A) p.positions[o++] = p.pos_base + i;
+        }
+      } else {
+        emit_range(tab, p, r, 0u, sr.t, x, o, end);
+      }
+    }
+    const uint2 c = p.ckpt[r * cpr + k];
+    if (c.x == kEmpty) continue;  // the piece ends inside the merged prefix
+    const uint32_t main_total = sr.count - sr.pre;
+    const uint32_t mu_next = k + 1 < cpr ? p.ckpt[r * cpr + k + 1].y : main_total;
+    if (mu_next == c.y) continue;  // no matches in the piece
+    const uint32_t from = (uint32_t)k * kCkptBytes > sr.t ? (uint32_t)k * kCkptBytes : sr.t;
+    const bool last = r == p.R - 1;
+    const uint32_t to = k + 1 < cpr ? (uint32_t)(k + 1) * kCkptBytes : (uint32_t)(p.S + (last ? p.tail : 0));
+    uint64_t o = sr.offset + sr.pre + c.y;
+    const uint64_t end0 = sr.offset + sr.pre + mu_next;
+    const uint64_t end = end0 < p.capacity ? end0 : p.capacity;
+    if (o >= end) continue;
+    uint32_t x = c.x;
+    emit_range(tab, p, r, from, to, x, o, end);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1721,11 +1822,12 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t stream) {
-  static std::atomic<size_t> limits[64];
+  static std::atomic<size_t> limits[64], limits_dense[64];
   // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
-  static std::atomic<uint64_t> choice[64];
-  auto kern = k_emit<LAYOUT, ESIZE>;
-  cudaError_t e = raise_smem_limit(kern, smem, limits);
+  static std::atomic<uint64_t> choice[64], choice_dense[64];
+  auto kern = p.ckpt_per_row ? k_emit_dense<LAYOUT, ESIZE> : k_emit<LAYOUT, ESIZE>;
+  std::atomic<uint64_t>* const chosen = p.ckpt_per_row ? choice_dense : choice;
+  cudaError_t e = raise_smem_limit(kern, smem, p.ckpt_per_row ? limits_dense : limits);
   if (e != cudaSuccess) return e;
   // One thread per row: the block size that keeps the most threads resident (the table in
   // shared memory is per block, so larger blocks share it among more rows), one wave of
@@ -1733,7 +1835,7 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
   int dev = 0;
   cudaGetDevice(&dev);
   int best_threads = 0, best_block = block, best_blocks = 1;
-  const uint64_t c = (dev >= 0 && dev < 64) ? choice[dev].load(std::memory_order_relaxed) : 0;
+  const uint64_t c = (dev >= 0 && dev < 64) ? chosen[dev].load(std::memory_order_relaxed) : 0;
   if (c && (c >> 24) == smem) {
     best_blocks = (int)((c >> 12) & 0xFFF);
     best_block = (int)(c & 0xFFF);
@@ -1748,11 +1850,12 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
       }
     }
     if (dev >= 0 && dev < 64 && best_blocks < 4096)
-      choice[dev].store((uint64_t)smem << 24 | (uint64_t)best_blocks << 12 | (uint64_t)best_block,
+      chosen[dev].store((uint64_t)smem << 24 | (uint64_t)best_blocks << 12 | (uint64_t)best_block,
                         std::memory_order_relaxed);
   }
-  // no more blocks than there are rows to cover: every block stages the table
-  const uint64_t need = (p.R + best_block - 1) / best_block;
+  // no more blocks than there are rows (or row pieces) to cover: every block stages the table
+  const uint64_t work = p.ckpt_per_row ? p.R * p.ckpt_per_row : p.R;
+  const uint64_t need = (work + best_block - 1) / best_block;
   const int blocks = (int)std::min<uint64_t>((uint64_t)grid * best_blocks, std::max<uint64_t>(need, 1));
   kern<<<blocks, best_block, smem, stream>>>(p);
   return cudaGetLastError();

@@ -216,6 +216,13 @@ def test_four_byte_stride_table(torch, n_sym, n_states):
     check(torch, spec, text[:77_777], opts=pm.MatchOpts(segment_bytes=128))
     clean = rng.integers(0, n_sym, size=250_001).astype(np.uint8)
     check(torch, spec, clean, offset=5)
+    # outside bytes next to the clamp boundaries of the four-at-once symbol clamp (K - 1,
+    # K, 127, 128, 128 + K - 1, 255 for K = n_sym + 1 classes) must all take the outside class
+    edge = np.array([n_sym, n_sym + 1, 6, 7, 127, 128, 128 + n_sym - 1, 128 + n_sym, 133, 255], np.uint8)
+    sprinkled = rng.integers(0, n_sym, size=200_001).astype(np.uint8)
+    where = rng.random(sprinkled.size) < 3e-4
+    sprinkled[where] = rng.choice(edge, size=int(where.sum()))
+    check(torch, spec, sprinkled, offset=1, opts=pm.MatchOpts(segment_bytes=512))
 
 
 @pytest.mark.parametrize("extra", [32, 200, None])
@@ -265,8 +272,8 @@ def test_sparse_counting_after_a_sparse_scan(torch):
 
 @pytest.mark.parametrize("seg", [0, 4160, 8192])
 def test_dense_emission(torch, seg):
-    # dense matches (10 %, then a stretch where every byte matches): every row replays its
-    # whole window; positions in order, with and without capacity truncation
+    # dense matches (10 %, then a stretch where every byte matches): positions in order,
+    # with and without capacity truncation
     spec = wl.dense_dfa()
     rng = np.random.default_rng(seg)
     text = rng.integers(0, 256, size=(6 << 20) + 4099).astype(np.uint8)
@@ -280,16 +287,24 @@ def test_dense_emission(torch, seg):
         tail[j] = first_acc[q]
         q = int(t[q, tail[j]])
     text[-(1 << 20):] = tail
-    dfa = load(spec)
     _, view = device_text(torch, text, 5)
     o = pm.MatchOpts(segment_bytes=seg)
     want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
     assert want.match_count > (text.size >> 6) + (1 << 20)
-    for cap in (want.match_count, want.match_count // 3):
-        pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
-        got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
-        assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, cap)
-        assert np.array_equal(pos.cpu().numpy().astype(np.uint64), want.positions[:cap])
+    # a fresh DFA emits row by row; once a scan of it has seen the density, pass 1
+    # writes a checkpoint every 2 KiB of each row and the emit pass works on the pieces in
+    # parallel (the first piece of a row starts at its merge point, the last row's tail
+    # belongs to its last piece)
+    for learn in (False, True):
+        dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+        if learn:
+            assert pm.parem_match_ex(dfa, view, None, o, length=text.size).match_count == want.match_count
+        for cap in (want.match_count, want.match_count // 3):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            got = pm.parem_match_ex(dfa, view, pos, o, length=text.size)
+            assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, cap)
+            assert np.array_equal(pos.cpu().numpy().astype(np.uint64), want.positions[:cap])
+        dfa.free()
 
 
 def test_host_buffers_in_pieces(torch):
