@@ -45,7 +45,8 @@ struct Scratch {
   size_t hdr_bytes = 0;
   uint32_t cur = 0;
   size_t used[2] = {0, 0};
-  DevResult* host_res = nullptr;  // pinned
+  DevResult* host_res = nullptr;  // pinned, mapped: the kernels write the result word here
+  DevResult* host_res_dev = nullptr;  // its device address
   void* dev_text = nullptr;       // staging for parem_match_host
   size_t text_bytes = 0;
   void* dev_pos = nullptr;
@@ -502,7 +503,15 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   Scratch* sc = get_scratch(dfa->device, stream);
   if (!sc) return PAREM_ERR_OOM;
   if (!sc->host_res) {
-    if (cudaMallocHost(&sc->host_res, sizeof(DevResult)) != cudaSuccess) return PAREM_ERR_OOM;
+    if (cudaHostAlloc(&sc->host_res, sizeof(DevResult), cudaHostAllocMapped) != cudaSuccess) {
+      sc->host_res = nullptr;
+      return PAREM_ERR_OOM;
+    }
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&sc->host_res_dev), sc->host_res, 0) != cudaSuccess) {
+      cudaFreeHost(sc->host_res);
+      sc->host_res = nullptr;
+      return PAREM_ERR_CUDA;
+    }
   }
   // header (double-buffered, see Scratch): [ticket 256][result 256][status K*8]
   const uint64_t o_status = 512;
@@ -569,6 +578,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.ticket = reinterpret_cast<uint32_t*>(hb);
   p.result = reinterpret_cast<DevResult*>(hb + 256);
   p.status = reinterpret_cast<unsigned long long*>(hb + o_status);
+  p.host_result = sc->host_res_dev;
   p.clear = reinterpret_cast<uint4*>(hb_other);
   p.clear_n16 = round_up(sc->used[sc->cur ^ 1u], 16) / 16;
   p.segrec = emit ? reinterpret_cast<SegRec*>(sb + o_segrec) : nullptr;
@@ -621,7 +631,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? PAREM_ERR_OOM : PAREM_ERR_CUDA;
   sc->used[sc->cur ^ 1u] = 0;
   sc->cur ^= 1u;
-  PAREM_CUDA_TRY(cudaMemcpyAsync(sc->host_res, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, stream));
+  // the last kernel's last block wrote the result word to host_res (publish_result)
   PAREM_CUDA_TRY(cudaStreamSynchronize(stream));
   const DevResult r = *sc->host_res;
   sc->stats.emit_replays = r.emit_replays;

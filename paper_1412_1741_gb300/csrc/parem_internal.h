@@ -119,6 +119,10 @@ struct SegRec {
 // Scratch bytes per row for recorded match positions (row-relative u32).
 constexpr uint32_t kRowSlotBytes = kRowSlots * 4;
 
+// Words of the ticket area (256 B at the start of a scan's header): the chunk ticket, then
+// the counters of blocks that finished pass 1 and the emit pass.
+constexpr uint32_t kDoneScanWord = 16, kDoneEmitWord = 32;
+
 // Result word filled on the device.
 struct DevResult {
   uint32_t final_state;  // compact
@@ -136,6 +140,7 @@ struct DevResult {
   unsigned long long cyc_spec, cyc_main, cyc_resolve;
   unsigned long long cyc_bitmap, cyc_lane;  // parts of cyc_spec: bitmap phase, lane phase
 };
+static_assert(sizeof(DevResult) % 8 == 0, "the result word is copied in 8-byte words");
 
 // Parameters of one plain scan (one text).
 struct ScanParams {
@@ -172,6 +177,8 @@ struct ScanParams {
   uint32_t* slot_end;      // R * cand_stride
   uint32_t* slot_cnt;      // R * cand_stride
   DevResult* result;
+  DevResult* host_result;  // host-mapped copy of *result, written by the last block of the
+                           // scan's last kernel (nullptr: the host copies the result itself)
   uint4* clear;            // zeroed by the kernel (clear_n16 16-byte words): the header
   uint64_t clear_n16;      // region of the previous scan, which the next scan reuses
   // outputs

@@ -1397,6 +1397,23 @@ __device__ __forceinline__ void drain_stages(const WarpCtx& wc, uint64_t budget)
 // Pass 1: speculation, main run, look-back.  P = candidate registers per lane when one row
 // is speculated by the whole warp (32 * P candidates); with P == 1, p.group lanes per row.
 // ---------------------------------------------------------------------------------------
+// The last block of a kernel to finish copies the result word to the host-mapped copy the
+// host reads after the stream synchronises (no separate device-to-host copy).  Every block
+// counts itself done after a fence, so the last one sees every block's result updates.
+__device__ __forceinline__ void publish_result(const ScanParams& p, uint32_t* done) {
+  if (p.host_result == nullptr) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.result);
+      volatile unsigned long long* dst = reinterpret_cast<volatile unsigned long long*>(p.host_result);
+      for (uint32_t i = 0; i < sizeof(DevResult) / 8; ++i) dst[i] = __ldcg(src + i);
+    }
+  }
+}
+
 // Zero the previous scan's header region (its ticket, result and status words), which the
 // next scan on the stream reuses; every thread of the grid takes a strided share.
 __device__ __forceinline__ void clear_prev_header(const ScanParams& p) {
@@ -1450,6 +1467,7 @@ __global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
   }
   flush_cycles(wc, p.result);
   drain_stages(wc, p.wait_budget);
+  publish_result(p, p.ticket + kDoneScanWord);
 }
 
 
@@ -1567,6 +1585,7 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
        r += (uint64_t)gridDim.x * blockDim.x)
     emit_row<LAYOUT, ESIZE>(tab, p, r);
+  publish_result(p, p.ticket + kDoneEmitWord);
 }
 
 // Dense emission: one thread per (row, piece of kCkptBytes).  Rows pass 1 flagged kCkptFlag
@@ -1627,6 +1646,7 @@ __global__ void __launch_bounds__(1024) k_emit_dense(const ScanParams p) {
     uint32_t x = c.x;
     emit_range(tab, p, r, from, to, x, o, end);
   }
+  publish_result(p, p.ticket + kDoneEmitWord);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1659,6 +1679,11 @@ __global__ void k_tiny(const ScanParams p) {
   }
   p.result->final_state = x;
   p.result->count = cnt;
+  if (p.host_result != nullptr) {  // one block, one thread: it wrote the word itself
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p.result);
+    volatile unsigned long long* dst = reinterpret_cast<volatile unsigned long long*>(p.host_result);
+    for (uint32_t i = 0; i < sizeof(DevResult) / 8; ++i) dst[i] = src[i];
+  }
 }
 
 #ifdef PAREM_BATCH_KERNELS  // compiled in parem_k_batch.cu only
