@@ -33,7 +33,7 @@ METRIC = "scanned GB/s on 1 GB300 (fraction of HBM peak); batched vs plain; p99 
 # the device code of the plain scan: DRAM counters taken on it stay valid while these are unchanged
 KERNEL_SOURCES = ["paper_1412_1741_gb300/csrc/parem_scan.cuh", "paper_1412_1741_gb300/csrc/parem_internal.h",
                   "paper_1412_1741_gb300/csrc/parem_k_byte.cu", "paper_1412_1741_gb300/csrc/parem_k_class.cu",
-                  "paper_1412_1741_gb300/csrc/parem_k_global.cu"]
+                  "paper_1412_1741_gb300/csrc/parem_k_global.cu", "paper_1412_1741_gb300/csrc/parem_k_win.cu"]
 
 CONFIGS = {
     "d2": dict(workload="sparse DFA: Aho-Corasick of 64 random keywords (len 8-24) over a-z+space, "
