@@ -307,8 +307,8 @@ void parem_batch_free(parem_batch* batch);
  * admission), plans them into the arena and launches the batch kernels on that arena's
  * stream.  With two or more arenas the next batch is launched while the previous one runs,
  * so requests that arrive meanwhile start as soon as thread blocks of the running batch
- * retire.  A completion thread waits for the batches in launch order and queues their
- * responses.  Nothing is allocated per request or per batch.  Mode PAREM_SERVE_FIFO instead
+ * retire.  A completion thread answers the batches as they finish, in any order (a batch
+ * holding a long request does not hold back later batches), and queues their responses.  Nothing is allocated per request or per batch.  Mode PAREM_SERVE_FIFO instead
  * runs the requests one at a time through parem_match, in arrival order (the plain
  * comparison).
  *

@@ -5,7 +5,7 @@
 // alone.  What the server adds is the choice of which requests share a launch:
 //
 //   submit -> pending (arrival order) --dispatcher--> batch in a free arena --stream-->
-//   completion thread (launch order) -> responses (poll queue, or a trace-replay sink)
+//   completion thread (whichever batch finished) -> responses (poll queue, or a replay sink)
 //
 // * Arenas: each holds one batch's device scratch, device descriptors, the pinned host image
 //   of the descriptors and the pinned result words, plus its own stream and event.  They are
@@ -245,7 +245,33 @@ void complete_batches(parem_server* s) {
   for (;;) {
     s->cv_done.wait(lk, [&] { return s->dispatcher_done || !s->inflight.empty(); });
     if (s->inflight.empty()) break;  // the dispatcher has stopped and nothing is left
-    Round& r = s->inflight.front();
+    // Rounds finish out of launch order (a batch holding one long request runs for long
+    // after later, short batches are done): answer whichever round has finished, so that
+    // short requests are not held behind a long one and its arena is free again at once.
+    size_t ready = s->inflight.size();
+    for (size_t k = 0; k < s->inflight.size(); ++k) {
+      const cudaError_t q = cudaEventQuery(s->arenas[s->inflight[k].arena].done);
+      if (q != cudaErrorNotReady) {
+        ready = k;
+        break;
+      }
+    }
+    if (ready == s->inflight.size()) {
+      if (s->inflight.size() == 1) {
+        // one round in flight: block on its event instead of polling
+        const int ai1 = s->inflight.front().arena;
+        lk.unlock();
+        cudaEventSynchronize(s->arenas[ai1].done);
+        lk.lock();
+      } else {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+      }
+      continue;
+    }
+    Round r = std::move(s->inflight[ready]);
+    s->inflight.erase(s->inflight.begin() + (std::ptrdiff_t)ready);
     const int ai = r.arena;
     parem_batch* b = r.batch;
     std::vector<Req> reqs = std::move(r.reqs);
@@ -264,7 +290,6 @@ void complete_batches(parem_server* s) {
     }
     batch_release(b);
     lk.lock();
-    s->inflight.pop_front();
     s->free_arenas.push_back(ai);
     deliver(s, reqs, resp);
     s->cv_dispatch.notify_one();

@@ -270,6 +270,44 @@ def test_sparse_counting_after_a_sparse_scan(torch):
     dfa.free()
 
 
+@pytest.mark.parametrize("offset,cap_div", [(0, 1), (7, 1), (3, 3)])
+def test_clustered_matches_after_a_sparse_scan(torch, offset, cap_div):
+    # a DFA whose last scan was sparse counts per vector (sparse counting); a text with a
+    # dense cluster of keywords (rows with more matches than pass 1 records), keywords at
+    # row starts (matches inside merged prefixes) and in the unaligned head must still give
+    # every position in order, with and without capacity truncation
+    kws = wl.random_keywords(24, 6, 12, seed=8)
+    sym = wl.letters_byte_map()
+    t, acc = wl.aho_corasick_dfa([[int(sym[b]) for b in kw] for kw in kws], 27)
+    spec = wl.DfaSpec(t, 0, acc, sym, "ac24-cluster", {"keywords": kws})
+    sparse = wl.zipf_words_text(4 << 20, seed_words=4, seed_plants=5, plant_rate=1e-5, keywords=kws)
+    text = wl.zipf_words_text(5 << 20, seed_words=6, seed_plants=7, plant_rate=2e-5, keywords=kws)
+    rng = np.random.default_rng(offset)
+    pos = 1000
+    while pos < 300_000:  # cluster: a keyword every ~20 bytes
+        kw = kws[int(rng.integers(len(kws)))]
+        text[pos:pos + len(kw)] = np.frombuffer(kw, np.uint8)
+        pos += len(kw) + int(rng.integers(1, 12))
+    for start in range(0, text.size - 64, 4096 * 7 + 64):  # keywords at scattered 64-aligned offsets
+        kw = kws[start % len(kws)]
+        text[start:start + len(kw)] = np.frombuffer(kw, np.uint8)
+    text[:len(kws[0])] = np.frombuffer(kws[0], np.uint8)  # a match inside the head bytes
+    dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    _, sview = device_text(torch, sparse, 0)
+    want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
+    assert want.match_count > 10_000
+    _, view = device_text(torch, text, offset)
+    for opts in (None, pm.MatchOpts(segment_bytes=1024), pm.MatchOpts(segment_bytes=128)):
+        # a sparse scan first, so that this scan of the clustered text counts sparsely
+        assert pm.parem_match(dfa, sview, length=sparse.size).match_count < 1024 * 4
+        cap = want.match_count // cap_div
+        pos_t = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+        got = pm.parem_match_ex(dfa, view, pos_t, opts, length=text.size)
+        assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, cap)
+        assert np.array_equal(pos_t.cpu().numpy().astype(np.uint64), want.positions[:cap])
+    dfa.free()
+
+
 @pytest.mark.parametrize("seg", [0, 4160, 8192])
 def test_dense_emission(torch, seg):
     # dense matches (10 %, then a stretch where every byte matches): positions in order,
