@@ -386,9 +386,13 @@ def run_serve(args, rank, world, local_rank):
     def summary(req, resp):
         lat = (resp["done_ns"] - resp["arrival_ns"]) / 1e6
         span = (resp["done_ns"].max() - resp["arrival_ns"].min()) / 1e9
+        queue = (resp["launch_ns"] - resp["arrival_ns"]) / 1e6  # waiting for a batch and an arena
+        run = (resp["done_ns"] - resp["launch_ns"]) / 1e6      # launch of its batch to its answer
         return {"requests": int(len(req)), "bytes": int(req["len"].sum()),
                 "gbs": round(float(req["len"].sum()) / span / 1e9, 2), "span_s": round(span, 3),
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "p50_queue_ms": round(float(np.percentile(queue, 50)), 3),
+                "p50_run_ms": round(float(np.percentile(run, 50)), 3),
                 "errors": int((resp["status"] != 0).sum())}
 
     srv = pm.parem_server_create(dfas, pm.ServerOpts(arenas=args.arenas))

@@ -308,7 +308,9 @@ void parem_batch_free(parem_batch* batch);
  * stream.  With two or more arenas the next batch is launched while the previous one runs,
  * so requests that arrive meanwhile start as soon as thread blocks of the running batch
  * retire.  A completion thread answers the batches as they finish, in any order (a batch
- * holding a long request does not hold back later batches), and queues their responses.  Nothing is allocated per request or per batch.  Mode PAREM_SERVE_FIFO instead
+ * holding a long request does not hold back later batches), and queues their responses;
+ * a request without a positions buffer is answered as soon as the kernel has its result,
+ * before the rest of its batch is done.  Nothing is allocated per request or per batch.  Mode PAREM_SERVE_FIFO instead
  * runs the requests one at a time through parem_match, in arrival order (the plain
  * comparison).
  *

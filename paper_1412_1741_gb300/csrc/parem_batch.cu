@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -41,6 +42,8 @@ struct parem_batch {
   void* scratch = nullptr;
   DevResult* host_res = nullptr;        // pinned, per sorted item
   DevResult* dev_res = nullptr;
+  EarlyResult* host_early = nullptr;    // arena's early results, per sorted item (or nullptr)
+  EarlyResult* dev_early = nullptr;
   BatchParams bp{};
   uint64_t zero_bytes = 0;
   int grid = 0, block = 0;
@@ -314,6 +317,12 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     }
     b->scratch = arena->scratch;
     b->host_res = arena->host_res;
+    if (arena->host_early && arena->dev_early) {
+      // the arena is idle: no kernel writes these slots while they are cleared
+      b->host_early = arena->host_early;
+      b->dev_early = arena->dev_early;
+      for (uint32_t k = 0; k < n; ++k) reinterpret_cast<volatile uint32_t*>(&b->host_early[k].ready)[0] = 0u;
+    }
   } else {
     if (cudaMalloc(&b->scratch, std::max<uint64_t>(off, 256)) != cudaSuccess) {
       release(b);
@@ -434,6 +443,7 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     p.slot_end = reinterpret_cast<uint32_t*>(sb + map_off[i]);
     p.slot_cnt = reinterpret_cast<uint32_t*>(sb + map_off[i] + pl.R * (uint64_t)p.cand_stride * 4);
     p.result = b->dev_res + k;
+    p.early = (!emit && b->dev_early) ? b->dev_early + k : nullptr;
     p.positions = emit ? it.positions : nullptr;
     p.capacity = emit ? it.capacity : 0;
     if (pl.R) {
@@ -751,6 +761,23 @@ int batch_sorted_result(const parem_batch* b, uint32_t k, parem_result* res) {
   res->match_count = r.count;
   res->n_written = (it.positions && it.capacity) ? std::min<uint64_t>(r.count, it.capacity) : 0;
   return (it.positions && it.capacity > 0 && r.count > it.capacity) ? PAREM_ERR_CAPACITY : PAREM_OK;
+}
+
+bool batch_early_result(const parem_batch* b, uint32_t k, parem_result* res) {
+  if (!b->host_early || k >= b->n_items) return false;
+  const volatile EarlyResult& e = b->host_early[k];
+  if (e.ready == 0) return false;
+  std::atomic_thread_fence(std::memory_order_acquire);
+  const uint32_t i = b->order[k];
+  const parem_batch_item& it = b->items[i];
+  if (it.len == 0 || e.error != 0 || (it.positions && it.capacity > 0)) return false;
+  const Prepared& P = it.dfa->host;
+  const uint32_t fs = e.final_state;
+  std::memset(res, 0, sizeof(*res));
+  res->final_state = fs < P.n ? P.orig_of[fs] : PAREM_NONE;
+  res->accepted = (fs < P.n && fs >= P.first_accept) ? 1 : 0;
+  res->match_count = e.count;
+  return true;
 }
 
 uint32_t batch_size(const parem_batch* b) { return b->n_items; }

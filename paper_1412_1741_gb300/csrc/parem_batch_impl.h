@@ -23,6 +23,8 @@ struct BatchArena {
   uint64_t desc_cap = 0;
   DevResult* host_res = nullptr;  // pinned host, res_cap entries
   uint32_t res_cap = 0;
+  EarlyResult* host_early = nullptr;  // pinned, mapped: res_cap early results (optional)
+  EarlyResult* dev_early = nullptr;   // its device address
   cudaStream_t stream = nullptr;
 };
 
@@ -37,6 +39,9 @@ void batch_release(parem_batch* b);
 // status (OK, CAPACITY, TIMEOUT or INTERNAL), and what it taught about the DFA's convergence.
 int batch_sorted_result(const parem_batch* b, uint32_t k, parem_result* res);
 int batch_item_result(const parem_batch* b, uint32_t i, parem_result* res);
+// While the batch runs: the result of the item at sorted position k if its kernel has
+// published it early (items without positions, arenas with early results); false otherwise.
+bool batch_early_result(const parem_batch* b, uint32_t k, parem_result* res);
 uint32_t batch_size(const parem_batch* b);
 uint32_t batch_kernels(const parem_batch* b);  // kernel launches of one batch_enqueue
 uint32_t batch_order(const parem_batch* b, uint32_t k);  // sorted position -> given index

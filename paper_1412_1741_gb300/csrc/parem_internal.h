@@ -142,6 +142,18 @@ struct DevResult {
 };
 static_assert(sizeof(DevResult) % 8 == 0, "the result word is copied in 8-byte words");
 
+// A batch item's result in host-mapped memory, written by the kernel that finishes the item
+// (its last chunk, or the tiny kernel) as soon as it is known, so that a server can answer
+// the request before the rest of its batch is done.  `ready` is written last, after a
+// system-scope fence.
+struct EarlyResult {
+  uint32_t final_state;  // compact
+  uint32_t error;
+  uint64_t count;
+  uint32_t ready;
+  uint32_t pad;
+};
+
 // Parameters of one plain scan (one text).
 struct ScanParams {
   DeviceDfa dfa;
@@ -179,6 +191,7 @@ struct ScanParams {
   DevResult* result;
   DevResult* host_result;  // host-mapped copy of *result, written by the last block of the
                            // scan's last kernel (nullptr: the host copies the result itself)
+  EarlyResult* early;      // batch items without positions: early copy of the result (or nullptr)
   uint4* clear;            // zeroed by the kernel (clear_n16 16-byte words): the header
   uint64_t clear_n16;      // region of the previous scan, which the next scan reuses
   // outputs

@@ -288,6 +288,15 @@ __device__ uint32_t run_bytes(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p, u
   return x;
 }
 
+// Early copy of a finished item's result for the host (see EarlyResult).
+__device__ __forceinline__ void write_early(EarlyResult* e, uint32_t final_state, uint64_t count, uint32_t error) {
+  e->final_state = final_state;
+  e->count = count;
+  e->error = error;
+  __threadfence_system();
+  *reinterpret_cast<volatile uint32_t*>(&e->ready) = 1u;
+}
+
 // Associative join of (dead, count) pairs in text order: everything after a death counts 0.
 struct Pfx {
   uint32_t dead;
@@ -1369,6 +1378,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   if (j == p.n_chunks - 1 && lane == 0) {
     p.result->final_state = inc.dead ? dead : E_chunk;
     p.result->count = inc.count;
+    if (p.early != nullptr) write_early(p.early, inc.dead ? dead : E_chunk, inc.count, read_error(p.result));
   }
 #if PAREM_PHASE_STATS
   if (lane == 0) {
@@ -1812,6 +1822,7 @@ __global__ void k_batch_tiny(const __grid_constant__ BatchParams bp, const uint3
   }
   p.result->final_state = x;
   p.result->count = cnt;
+  if (p.early != nullptr) write_early(p.early, x, cnt, 0u);
 }
 
 #endif  // PAREM_BATCH_KERNELS

@@ -64,6 +64,8 @@ struct Round {
   parem_batch* batch = nullptr;
   std::vector<Req> reqs;  // in the batch's given order
   int64_t launch_ns = 0;
+  std::vector<uint8_t> answered;  // per sorted position: answered early
+  uint32_t n_answered = 0;
 };
 
 }  // namespace
@@ -169,6 +171,7 @@ void launch_round(parem_server* s, int ai, std::vector<Req>& take, std::unique_l
     round.batch = b;
     round.reqs = std::move(take);
     round.launch_ns = t;
+    round.answered.assign(batch_size(b), 0);
     const uint32_t nk = batch_kernels(b);
     lk.lock();
     s->stats.batches++;
@@ -256,37 +259,60 @@ void complete_batches(parem_server* s) {
         break;
       }
     }
+    // requests whose results their kernels have already published (count-only requests):
+    // answered now, before the rest of their batch
+    bool early = false;
     if (ready == s->inflight.size()) {
-      if (s->inflight.size() == 1) {
-        // one round in flight: block on its event instead of polling
-        const int ai1 = s->inflight.front().arena;
-        lk.unlock();
-        cudaEventSynchronize(s->arenas[ai1].done);
-        lk.lock();
-      } else {
-        lk.unlock();
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-        lk.lock();
+      const int64_t t = now_ns();
+      for (Round& r : s->inflight) {
+        if (r.n_answered == r.answered.size()) continue;
+        std::vector<Req> reqs;
+        std::vector<parem_response> resp;
+        const uint32_t n = batch_size(r.batch);
+        for (uint32_t k = 0; k < n; ++k) {
+          if (r.answered[k]) continue;
+          parem_result res;
+          if (!batch_early_result(r.batch, k, &res)) continue;
+          const uint32_t i = batch_order(r.batch, k);
+          r.answered[k] = 1;
+          r.n_answered++;
+          reqs.push_back(r.reqs[i]);
+          resp.push_back(make_response(r.reqs[i], PAREM_OK, n, res, r.launch_ns, t));
+        }
+        if (!reqs.empty()) {
+          deliver(s, reqs, resp);
+          early = true;
+        }
       }
+    }
+    if (early) continue;
+    if (ready == s->inflight.size()) {
+      // nothing finished: poll again shortly (early results arrive while batches run)
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
       continue;
     }
     Round r = std::move(s->inflight[ready]);
     s->inflight.erase(s->inflight.begin() + (std::ptrdiff_t)ready);
     const int ai = r.arena;
     parem_batch* b = r.batch;
-    std::vector<Req> reqs = std::move(r.reqs);
     const int64_t launch = r.launch_ns;
     lk.unlock();
     const bool ok = cudaEventSynchronize(s->arenas[ai].done) == cudaSuccess;
     const int64_t t = now_ns();
     const uint32_t n = batch_size(b);
-    std::vector<parem_response> resp(reqs.size());
+    std::vector<Req> reqs;
+    std::vector<parem_response> resp;
     for (uint32_t k = 0; k < n; ++k) {
       const uint32_t i = batch_order(b, k);
       parem_result res;
+      // the final result also teaches the DFA's convergence hints, answered early or not
       int rc = ok ? batch_sorted_result(b, k, &res) : PAREM_ERR_CUDA;
+      if (r.answered[k]) continue;
       if (rc != PAREM_OK && rc != PAREM_ERR_CAPACITY) std::memset(&res, 0, sizeof(res));
-      resp[i] = make_response(reqs[i], rc, n, res, launch, t);
+      reqs.push_back(r.reqs[i]);
+      resp.push_back(make_response(r.reqs[i], rc, n, res, launch, t));
     }
     batch_release(b);
     lk.lock();
@@ -304,6 +330,7 @@ void destroy(parem_server* s) {
     if (A.a.desc) cudaFree(A.a.desc);
     if (A.a.host_desc) cudaFreeHost(A.a.host_desc);
     if (A.a.host_res) cudaFreeHost(A.a.host_res);
+    if (A.a.host_early) cudaFreeHost(A.a.host_early);
   }
   if (s->fifo_stream) cudaStreamDestroy(s->fifo_stream);
   delete s;
@@ -386,7 +413,9 @@ extern "C" int parem_server_create(parem_dfa* const* dfas, uint32_t n_dfas, cons
       bool ok = cudaMalloc(&A.a.scratch, scratch) == cudaSuccess &&
                 cudaMalloc(&A.a.desc, desc) == cudaSuccess &&
                 cudaMallocHost(&A.a.host_desc, desc) == cudaSuccess &&
-                cudaMallocHost(&A.a.host_res, sizeof(DevResult) * max_items) == cudaSuccess;
+                cudaMallocHost(&A.a.host_res, sizeof(DevResult) * max_items) == cudaSuccess &&
+                cudaHostAlloc(&A.a.host_early, sizeof(EarlyResult) * max_items, cudaHostAllocMapped) == cudaSuccess &&
+                cudaHostGetDevicePointer(reinterpret_cast<void**>(&A.a.dev_early), A.a.host_early, 0) == cudaSuccess;
       if (!ok) {
         destroy(s);
         return PAREM_ERR_OOM;
