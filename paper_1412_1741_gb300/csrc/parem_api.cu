@@ -544,9 +544,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
-  const uint32_t cpr = (emit && pl.dense && pl.R) ? (uint32_t)((pl.S + kCkptBytes - 1) / kCkptBytes) : 0u;
-  const uint64_t o_ckpt = round_up(o_slot + 2 * slot_bytes, 256);
-  const uint64_t total = round_up(std::max<uint64_t>(o_ckpt + pl.R * (uint64_t)cpr * 8, 256), 256);
+  const uint64_t total = round_up(std::max<uint64_t>(o_slot + 2 * slot_bytes, 256), 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
   uint8_t* sb = static_cast<uint8_t*>(sc->dev);
@@ -585,8 +583,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
-  p.ckpt_per_row = cpr;
-  p.ckpt = cpr ? reinterpret_cast<uint2*>(sb + o_ckpt) : nullptr;
+  p.stream_emit = (emit && pl.dense && pl.R) ? 1u : 0u;
   p.positions = emit ? positions : nullptr;
   p.capacity = emit ? capacity : 0;
 
@@ -621,7 +618,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
     if (e == cudaSuccess && emit) {
       sc->emitted = true;
       const DevProps props = dev_props(dfa->device);
-      e = launch_emit_dispatch(P.layout, P.esize, p, props.sms, 256, small_smem, stream);
+      e = launch_emit_dispatch(P.layout, P.esize, p, &tm, props.sms, 256, small_smem, stream);
     }
   }
   if (e == cudaSuccess && timed && pl.R == 0) e = cudaEventRecord(sc->ev[1], stream);

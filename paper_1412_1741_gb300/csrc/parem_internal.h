@@ -22,9 +22,6 @@ constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4 + 48;
 constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
 constexpr uint32_t kSlotsFlag = 2u;      // SegRec.flags: every main-run match of the row is in its slots
 constexpr uint32_t kPreFlag = 4u;        // SegRec.flags: replay the merged prefix [0, t) from x
-constexpr uint32_t kCkptFlag = 8u;       // SegRec.flags: the main run [t, end) is emitted in pieces
-                                         // from the checkpoints pass 1 wrote (dense matches)
-constexpr uint32_t kCkptBytes = 2048;    // bytes between checkpoints of a row
 constexpr uint32_t kRowSlots = 16;       // match positions pass 1 records per row
 constexpr uint64_t kMaxText = 1ull << 45;
 
@@ -119,9 +116,9 @@ struct SegRec {
 // Scratch bytes per row for recorded match positions (row-relative u32).
 constexpr uint32_t kRowSlotBytes = kRowSlots * 4;
 
-// Words of the ticket area (256 B at the start of a scan's header): the chunk ticket, then
-// the counters of blocks that finished pass 1 and the emit pass.
-constexpr uint32_t kDoneScanWord = 16, kDoneEmitWord = 32;
+// Words of the ticket area (256 B at the start of a scan's header): the chunk ticket, the
+// counters of blocks that finished pass 1 and the emit pass, the streaming emit's ticket.
+constexpr uint32_t kDoneScanWord = 16, kDoneEmitWord = 32, kEmitTicketWord = 48;
 
 // Result word filled on the device.
 struct DevResult {
@@ -176,9 +173,8 @@ struct ScanParams {
   uint64_t pos_base;       // added to every position written (text offset of a piece)
   uint32_t sparse_count;   // main run: track the largest state of each 16-byte vector and
                            // count (by a replay of the vector) only where it is accepting
-  uint32_t ckpt_per_row;   // dense emission: checkpoints per row (0: off), one per kCkptBytes
-  uint2* ckpt;             // R * ckpt_per_row (state, main-run matches before the piece);
-                           // state kEmpty for pieces that end inside the merged prefix
+  uint32_t stream_emit;    // dense matches: the emit pass streams the rows through shared
+                           // memory by TMA as pass 1 does (k_emit_stream)
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch

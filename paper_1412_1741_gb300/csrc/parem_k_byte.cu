@@ -18,9 +18,10 @@ cudaError_t scan_byte(uint32_t esize, uint32_t P, const CUtensorMap& tm, const S
   }
 }
 
-cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return esize == 1 ? launch_emit<kByteSmem, 1>(p, grid, block, smem, s)
-                    : launch_emit<kByteSmem, 2>(p, grid, block, smem, s);
+cudaError_t emit_byte(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                      int grid, int block, size_t smem, cudaStream_t s) {
+  return esize == 1 ? launch_emit<kByteSmem, 1>(p, tm, grid, block, smem, s)
+                    : launch_emit<kByteSmem, 2>(p, tm, grid, block, smem, s);
 }
 
 cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s) {
@@ -37,8 +38,9 @@ cudaError_t scan_byte_stride(const CUtensorMap& tm, const ScanParams& p, int gri
   return launch_spec_scan<kByteStride, 1, 1>(tm, p, grid, block, smem, s);
 }
 
-cudaError_t emit_byte_stride(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return launch_emit<kByteStride, 1>(p, grid, block, smem, s);
+cudaError_t emit_byte_stride(const ScanParams& p, const CUtensorMap* tm,
+                             int grid, int block, size_t smem, cudaStream_t s) {
+  return launch_emit<kByteStride, 1>(p, tm, grid, block, smem, s);
 }
 
 cudaError_t tiny_byte_stride(const ScanParams& p, size_t smem, cudaStream_t s) {

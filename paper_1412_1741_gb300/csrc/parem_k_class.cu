@@ -29,13 +29,15 @@ cudaError_t scan_class_wide(uint32_t P, const CUtensorMap& tm, const ScanParams&
   }
 }
 
-cudaError_t emit_class(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return esize == 1 ? launch_emit<kClassSmem, 1>(p, grid, block, smem, s)
-                    : launch_emit<kClassSmem, 2>(p, grid, block, smem, s);
+cudaError_t emit_class(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                       int grid, int block, size_t smem, cudaStream_t s) {
+  return esize == 1 ? launch_emit<kClassSmem, 1>(p, tm, grid, block, smem, s)
+                    : launch_emit<kClassSmem, 2>(p, tm, grid, block, smem, s);
 }
 
-cudaError_t emit_class_wide(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return launch_emit<kClassSmemW, 2>(p, grid, block, smem, s);
+cudaError_t emit_class_wide(const ScanParams& p, const CUtensorMap* tm,
+                            int grid, int block, size_t smem, cudaStream_t s) {
+  return launch_emit<kClassSmemW, 2>(p, tm, grid, block, smem, s);
 }
 
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s) {

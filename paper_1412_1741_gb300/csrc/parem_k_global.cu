@@ -23,9 +23,10 @@ cudaError_t scan_global(uint32_t wide, uint32_t P, const CUtensorMap& tm, const 
   }
 }
 
-cudaError_t emit_global(uint32_t wide, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return wide ? launch_emit<kClassGlobalW, 2>(p, grid, block, smem, s)
-              : launch_emit<kClassGlobal, 2>(p, grid, block, smem, s);
+cudaError_t emit_global(uint32_t wide, const ScanParams& p, const CUtensorMap* tm,
+                        int grid, int block, size_t smem, cudaStream_t s) {
+  return wide ? launch_emit<kClassGlobalW, 2>(p, tm, grid, block, smem, s)
+              : launch_emit<kClassGlobal, 2>(p, tm, grid, block, smem, s);
 }
 
 cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s) {
@@ -48,16 +49,16 @@ cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, co
   }
 }
 
-cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, int grid, int block,
-                                 size_t smem, cudaStream_t s) {
+cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                                 int grid, int block, size_t smem, cudaStream_t s) {
   switch (layout) {
-    case kByteSmem: return emit_byte(esize, p, grid, block, smem, s);
-    case kByteStride: return emit_byte_stride(p, grid, block, smem, s);
-    case kClassWin: return emit_win(esize, p, grid, block, smem, s);
-    case kClassSmem: return emit_class(esize, p, grid, block, smem, s);
-    case kClassSmemW: return emit_class_wide(p, grid, block, smem, s);
-    case kClassGlobal: return emit_global(0, p, grid, block, smem, s);
-    default: return emit_global(1, p, grid, block, smem, s);
+    case kByteSmem: return emit_byte(esize, p, tm, grid, block, smem, s);
+    case kByteStride: return emit_byte_stride(p, tm, grid, block, smem, s);
+    case kClassWin: return emit_win(esize, p, tm, grid, block, smem, s);
+    case kClassSmem: return emit_class(esize, p, tm, grid, block, smem, s);
+    case kClassSmemW: return emit_class_wide(p, tm, grid, block, smem, s);
+    case kClassGlobal: return emit_global(0, p, tm, grid, block, smem, s);
+    default: return emit_global(1, p, tm, grid, block, smem, s);
   }
 }
 

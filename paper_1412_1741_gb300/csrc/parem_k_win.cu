@@ -19,9 +19,10 @@ cudaError_t scan_win(uint32_t esize, uint32_t P, const CUtensorMap& tm, const Sc
   }
 }
 
-cudaError_t emit_win(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-  return esize == 1 ? launch_emit<kClassWin, 1>(p, grid, block, smem, s)
-                    : launch_emit<kClassWin, 2>(p, grid, block, smem, s);
+cudaError_t emit_win(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                     int grid, int block, size_t smem, cudaStream_t s) {
+  return esize == 1 ? launch_emit<kClassWin, 1>(p, tm, grid, block, smem, s)
+                    : launch_emit<kClassWin, 2>(p, tm, grid, block, smem, s);
 }
 
 cudaError_t tiny_win(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s) {

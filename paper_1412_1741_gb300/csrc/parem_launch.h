@@ -59,8 +59,8 @@ struct Plan {
   uint32_t spec_cap;
   uint32_t serial;       // unmerged rows run from their resolved start (no slot maps)
   uint32_t sparse;       // count matches per 16-byte vector only where one occurs
-  uint32_t dense;        // matches were dense in the DFA's last large scan: emit positions in
-                         // pieces from checkpoints pass 1 writes
+  uint32_t dense;        // matches were dense in the DFA's last large scan: the emit pass
+                         // streams the rows through shared memory (k_emit_stream)
 };
 
 // The launch plan of one scan (parem_api.cu).
@@ -68,8 +68,8 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
 
 cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, const CUtensorMap& tm,
                                  const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, int grid, int block,
-                                 size_t smem, cudaStream_t s);
+cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                                 int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanParams& p, size_t smem,
                                  cudaStream_t s);
 
@@ -82,18 +82,24 @@ cudaError_t scan_class_wide(uint32_t P, const CUtensorMap& tm, const ScanParams&
                             size_t smem, cudaStream_t s);
 cudaError_t scan_global(uint32_t wide, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid,
                         int block, size_t smem, cudaStream_t s);
-cudaError_t emit_byte(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t emit_class(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t emit_class_wide(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
-cudaError_t emit_global(uint32_t wide, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_byte(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                      int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_class(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                       int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_class_wide(const ScanParams& p, const CUtensorMap* tm,
+                            int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_global(uint32_t wide, const ScanParams& p, const CUtensorMap* tm,
+                        int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_byte(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t scan_byte_stride(const CUtensorMap& tm, const ScanParams& p, int grid, int block, size_t smem,
                              cudaStream_t s);
-cudaError_t emit_byte_stride(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_byte_stride(const ScanParams& p, const CUtensorMap* tm,
+                             int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_byte_stride(const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t scan_win(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid, int block,
                      size_t smem, cudaStream_t s);
-cudaError_t emit_win(uint32_t esize, const ScanParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t emit_win(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
+                     int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_win(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class_wide(const ScanParams& p, size_t smem, cudaStream_t s);

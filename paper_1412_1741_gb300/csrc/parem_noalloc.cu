@@ -148,7 +148,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
     if (e == cudaSuccess && emit) {
       int sms = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAREM_ERR_CUDA;
-      e = launch_emit_dispatch(P.layout, P.esize, p, sms, 256, small_smem, st);
+      e = launch_emit_dispatch(P.layout, P.esize, p, &tm, sms, 256, small_smem, st);
     }
   }
   if (e != cudaSuccess) return PAREM_ERR_CUDA;

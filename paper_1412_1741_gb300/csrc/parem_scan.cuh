@@ -962,14 +962,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
   const bool run = active && my_conv;
   uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
-  if (p.ckpt_per_row && run) {
-    // dense emission: pieces that end inside the merged prefix have no main-run state; the
-    // piece holding the merge point t starts there (state my_sigma, no matches before it)
-    const uint32_t kt = my_t / kCkptBytes;
-    for (uint32_t k = 0; k < kt && k < p.ckpt_per_row; ++k)
-      p.ckpt[myrow * p.ckpt_per_row + k] = make_uint2(kEmpty, 0u);
-    if (kt < p.ckpt_per_row) p.ckpt[myrow * p.ckpt_per_row + kt] = make_uint2(my_sigma, 0u);
-  }
   for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
     const uint32_t b = blk % kStages;
     const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
@@ -997,9 +989,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
     if (run) {
       const uint32_t col0 = blk * kBox;
-      // dense emission: the state and the count at each later piece start
-      if (p.ckpt_per_row && col0 % kCkptBytes == 0 && col0 > my_t)
-        p.ckpt[myrow * p.ckpt_per_row + col0 / kCkptBytes] = make_uint2(s, mu);
 #pragma unroll
       for (uint32_t i = 0; i < kBox / 16; ++i) {
         const uint32_t col = col0 + i * 16u;
@@ -1367,10 +1356,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         sr.ls = ls;
         // every main-run match was recorded by pass 1: the emit pass only copies them
         if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
-        else if (main_live && p.ckpt_per_row && my_t < p.S) {
-          sr.flags |= kCkptFlag;
-          sr.t = my_t;  // the first piece starts at the merge point
-        }
       }
       p.segrec[myrow] = sr;
     }
@@ -1498,10 +1483,15 @@ __device__ __forceinline__ void emit_range(const Tab<LAYOUT, ESIZE>& tab, const 
   // of a vector collect a 16-bit mask of accepting positions, written after the vector
   // (one store per match instead of a predicated store at every byte)
   if ((off & 15u) == 0 && off + 16 <= p.S && off + 16 <= to) {
+    // two vectors in flight ahead of the one consumed (a replay is a single dependent chain
+    // per thread: the loads must cover the memory latency on their own)
+    const uint4 zero = make_uint4(0, 0, 0, 0);
     uint4 nxt = ldg16(rowp + off);
+    uint4 nxt2 = (off + 32 <= p.S && off + 32 <= to) ? ldg16(rowp + off + 16) : zero;
     while (off + 16 <= p.S && off + 16 <= to && o < end) {
       const uint4 v = nxt;
-      if (off + 32 <= p.S && off + 32 <= to) nxt = ldg16(rowp + off + 16);
+      nxt = nxt2;
+      if (off + 48 <= p.S && off + 48 <= to) nxt2 = ldg16(rowp + off + 32);
       uint32_t m = 0;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -1598,64 +1588,157 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   publish_result(p, p.ticket + kDoneEmitWord);
 }
 
-// Dense emission: one thread per (row, piece of kCkptBytes).  Rows pass 1 flagged kCkptFlag
-// replay each piece [max(k kCkptBytes, t), next piece) from the state recorded at its start
-// and write its matches at the row's offset + the prefix's matches + the main-run matches
-// before the piece; the thread of piece 0 also writes the head or prefix matches.  Other
-// rows are emitted whole by the thread of piece 0.
+// Dense emission, streamed: warps take chunk tickets as in pass 1 and the chunk's rows arrive
+// through the same TMA stages; each lane replays its row's match window [fv, lv) from the
+// state pass 1 recorded at fv, collecting per 16-byte vector a mask of accepting steps from
+// which it writes positions at the row's offset.  The head or merged-prefix matches (before
+// the window) and the last row's tail (after the last full row) are replayed from global
+// memory by the lane; rows whose matches pass 1 recorded are copied.
 template <int LAYOUT, int ESIZE>
-__global__ void __launch_bounds__(1024) k_emit_dense(const ScanParams p) {
+__global__ void __launch_bounds__(1024, 1)
+    k_emit_stream(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
-  const DeviceDfa& D = p.dfa;
-  load_tables<LAYOUT, ESIZE>(sm, D);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  load_tables<LAYOUT, ESIZE>(sm, p.dfa);
+  const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
+  WarpCtx wc;
+  wc.sm = sm;
+  wc.lane = lane;
+  wc.stage0 = region + warp * (kStages * kStageBytes);
+  wc.bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
+  wc.phase_bits = 0;
+  wc.pending = 0;
+  if (lane == 0) {
+    for (uint32_t b = 0; b < kStages; ++b) mbar_init(smem_u32(sm + wc.bar0 + 8 * b), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
   __syncthreads();
   Tab<LAYOUT, ESIZE> tab;
   tab.sm = sm;
-  tab.gtable = D.table;
-  tab.rowbytes = D.rowbytes;
+  tab.gtable = p.dfa.table;
+  tab.rowbytes = p.dfa.rowbytes;
   tab.smem_tier = 1;
   tab.set_win(p.dfa.win);
-  const uint32_t A = D.first_accept;
-  const uint64_t cpr = p.ckpt_per_row;
-  const uint64_t items = p.R * cpr;
-  for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < items;
-       it += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t r = it / cpr, k = it % cpr;
-    const SegRec sr = p.segrec[r];
-    if (sr.count == 0 || sr.offset >= p.capacity) continue;
-    if (!(sr.flags & kCkptFlag)) {
-      if (k == 0) emit_row<LAYOUT, ESIZE>(tab, p, r);
-      continue;
-    }
-    if (k == 0 && (sr.flags & (kHeadFlag | kPreFlag))) {
-      const uint64_t end = (sr.offset + sr.pre < p.capacity) ? sr.offset + sr.pre : p.capacity;
-      uint64_t o = sr.offset;
-      uint32_t x = sr.x;
-      if (sr.flags & kHeadFlag) {
-        for (uint64_t i = 0; i < p.h && o < end; ++i) {
-          x = tab.next(x, tab.col(ldg8(p.text + i)));
-          if (x >= A) p.positions[o++] = p.pos_base + i;
+  const uint32_t A = p.dfa.first_accept;
+  const uint32_t nblk = (uint32_t)(p.S / kBox);
+  uint32_t* const tickets = p.ticket + kEmitTicketWord;
+  bool failed = false;
+  for (;;) {
+    uint32_t ticket = 0;
+    if (lane == 0) ticket = read_error(p.result) ? 0xFFFFFFFFu : atomicAdd(tickets, 1u);
+    ticket = __shfl_sync(kFull, ticket, 0);
+    if ((uint64_t)ticket >= p.n_chunks) break;
+    const uint64_t row0 = (uint64_t)ticket * kLanes;
+    const uint64_t r = row0 + lane;
+    // this lane's window [fv, lv) with its state x and output range [o, end)
+    uint32_t fv = kEmpty, lv = 0, x = 0;
+    uint64_t o = 0, end = 0;
+    if (r < p.R) {
+      const SegRec sr = p.segrec[r];
+      if (sr.count > 0 && sr.offset < p.capacity) {
+        end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
+        o = sr.offset;
+        if (sr.flags & kHeadFlag) {
+          uint32_t y = sr.x;
+          for (uint64_t i = 0; i < p.h && o < end; ++i) {
+            y = tab.next(y, tab.col(ldg8(p.text + i)));
+            if (y >= A) p.positions[o++] = p.pos_base + i;
+          }
+        } else if (sr.flags & kPreFlag) {
+          uint32_t y = sr.x;
+          emit_range(tab, p, r, 0u, sr.t, y, o, end);
         }
-      } else {
-        emit_range(tab, p, r, 0u, sr.t, x, o, end);
+        if (o < end && sr.lv > 0) {
+          if (sr.flags & kSlotsFlag) {
+            const uint64_t gbase = p.pos_base + p.h + r * p.S;
+            const uint32_t* sl = p.slots + r * kRowSlots;
+            for (uint32_t i = 0; o < end; ++i) p.positions[o++] = gbase + sl[i];
+          } else {
+            fv = sr.fv;
+            lv = sr.lv;
+            x = sr.fs;
+          }
+        }
       }
     }
-    const uint2 c = p.ckpt[r * cpr + k];
-    if (c.x == kEmpty) continue;  // the piece ends inside the merged prefix
-    const uint32_t main_total = sr.count - sr.pre;
-    const uint32_t mu_next = k + 1 < cpr ? p.ckpt[r * cpr + k + 1].y : main_total;
-    if (mu_next == c.y) continue;  // no matches in the piece
-    const uint32_t from = (uint32_t)k * kCkptBytes > sr.t ? (uint32_t)k * kCkptBytes : sr.t;
-    const bool last = r == p.R - 1;
-    const uint32_t to = k + 1 < cpr ? (uint32_t)(k + 1) * kCkptBytes : (uint32_t)(p.S + (last ? p.tail : 0));
-    uint64_t o = sr.offset + sr.pre + c.y;
-    const uint64_t end0 = sr.offset + sr.pre + mu_next;
-    const uint64_t end = end0 < p.capacity ? end0 : p.capacity;
-    if (o >= end) continue;
-    uint32_t x = c.x;
-    emit_range(tab, p, r, from, to, x, o, end);
+    // the blocks that hold some lane's window inside the full rows
+    uint32_t fmin = fv, lmax = (fv == kEmpty) ? 0u : lv;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      fmin = min(fmin, __shfl_xor_sync(kFull, fmin, d));
+      lmax = max(lmax, __shfl_xor_sync(kFull, lmax, d));
+    }
+    if (fmin == kEmpty) continue;
+    const uint32_t b0 = fmin / kBox;
+    const uint32_t b1 = min((lmax + kBox - 1) / kBox, nblk);
+    const uint32_t in_row_end = min(lv, (uint32_t)p.S);
+    if (b0 < b1) {
+      const uint32_t nb = b1 - b0;
+      const uint32_t first = nb < kStages ? nb : kStages;
+      if (lane == 0) {
+        for (uint32_t k = 0; k < first; ++k) {
+          const uint32_t bar = smem_u32(sm + wc.bar0 + 8 * k);
+          mbar_arrive_expect_tx(bar, kStageBytes);
+          tma_load_2d(smem_u32(sm + wc.stage0 + k * kStageBytes), &tmap, bar, (int32_t)((b0 + k) * kBox),
+                      (int32_t)row0);
+        }
+      }
+      wc.pending |= (1u << first) - 1u;
+      for (uint32_t k = 0; k < nb; ++k) {
+        const uint32_t b = k % kStages;
+        const uint32_t bar = smem_u32(sm + wc.bar0 + 8 * b);
+        if (!stage_wait(bar, (wc.phase_bits >> b) & 1u, p.wait_budget, p.result)) {
+          set_error(p.result, kErrTimeout);
+          failed = true;
+          break;
+        }
+        wc.phase_bits ^= 1u << b;
+        wc.pending &= ~(1u << b);
+        uint4 v[kBox / 16];
+        const uint8_t* stg = sm + wc.stage0 + b * kStageBytes + lane * kBox;
+#pragma unroll
+        for (uint32_t i = 0; i < kBox / 16; ++i)
+          v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane >> 1) & 3u)) * 16u));
+        __syncwarp();
+        if (k + kStages < nb) {
+          if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(bar, kStageBytes);
+            tma_load_2d(smem_u32(sm + wc.stage0 + b * kStageBytes), &tmap, bar, (int32_t)((b0 + k + kStages) * kBox),
+                        (int32_t)row0);
+          }
+          wc.pending |= 1u << b;
+        }
+        const uint32_t col0 = (b0 + k) * kBox;
+        const uint64_t pb = p.pos_base + p.h + r * p.S + col0;
+#pragma unroll
+        for (uint32_t i = 0; i < kBox / 16; ++i) {
+          const uint32_t col = col0 + i * 16u;
+          if (col >= fv && col + 16u <= in_row_end && o < end) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              x = tab.next(x, tab.col(byte_of(v[i], q)));
+              m |= (x >= A ? 1u : 0u) << q;
+            }
+            while (m != 0 && o < end) {
+              p.positions[o++] = pb + i * 16u + (uint32_t)(__ffs(m) - 1);
+              m &= m - 1u;
+            }
+          }
+        }
+      }
+      if (failed) break;
+    }
+    // the last row's window past the last full row (its tail)
+    if (fv != kEmpty && lv > p.S && o < end) {
+      const uint32_t from = fv > (uint32_t)p.S ? fv : (uint32_t)p.S;
+      emit_range(tab, p, r, from, lv, x, o, end);
+    }
   }
+  drain_stages(wc, p.wait_budget);
   publish_result(p, p.ticket + kDoneEmitWord);
 }
 
@@ -1857,13 +1940,32 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 }
 
 template <int LAYOUT, int ESIZE>
-cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, cudaStream_t stream) {
-  static std::atomic<size_t> limits[64], limits_dense[64];
+cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, int block, size_t smem,
+                        cudaStream_t stream) {
+  static std::atomic<size_t> limits[64], limits_stream[64];
   // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
-  static std::atomic<uint64_t> choice[64], choice_dense[64];
-  auto kern = p.ckpt_per_row ? k_emit_dense<LAYOUT, ESIZE> : k_emit<LAYOUT, ESIZE>;
-  std::atomic<uint64_t>* const chosen = p.ckpt_per_row ? choice_dense : choice;
-  cudaError_t e = raise_smem_limit(kern, smem, p.ckpt_per_row ? limits_dense : limits);
+  static std::atomic<uint64_t> choice[64];
+  if (p.stream_emit && tm != nullptr) {
+    // dense matches: pass 1's launch shape (one block per SM, warps as shared memory allows)
+    auto kern = k_emit_stream<LAYOUT, ESIZE>;
+    const size_t per_warp = kStages * kStageBytes + kStages * 8;
+    const size_t fixed = smem + 1024;  // column map and table, then alignment of the stages
+    int optin = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int warps = (int)std::min<size_t>(32, ((size_t)optin - fixed) / per_warp);
+    if (warps < 1) return cudaErrorInvalidValue;
+    const size_t sm_bytes = fixed + (size_t)warps * per_warp;
+    cudaError_t e = raise_smem_limit(kern, sm_bytes, limits_stream);
+    if (e != cudaSuccess) return e;
+    const uint64_t chunk_blocks = (p.n_chunks + warps - 1) / warps;
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, chunk_blocks));
+    kern<<<blocks, warps * 32, sm_bytes, stream>>>(*tm, p);
+    return cudaGetLastError();
+  }
+  auto kern = k_emit<LAYOUT, ESIZE>;
+  cudaError_t e = raise_smem_limit(kern, smem, limits);
   if (e != cudaSuccess) return e;
   // One thread per row: the block size that keeps the most threads resident (the table in
   // shared memory is per block, so larger blocks share it among more rows), one wave of
@@ -1871,7 +1973,7 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
   int dev = 0;
   cudaGetDevice(&dev);
   int best_threads = 0, best_block = block, best_blocks = 1;
-  const uint64_t c = (dev >= 0 && dev < 64) ? chosen[dev].load(std::memory_order_relaxed) : 0;
+  const uint64_t c = (dev >= 0 && dev < 64) ? choice[dev].load(std::memory_order_relaxed) : 0;
   if (c && (c >> 24) == smem) {
     best_blocks = (int)((c >> 12) & 0xFFF);
     best_block = (int)(c & 0xFFF);
@@ -1886,12 +1988,11 @@ cudaError_t launch_emit(const ScanParams& p, int grid, int block, size_t smem, c
       }
     }
     if (dev >= 0 && dev < 64 && best_blocks < 4096)
-      chosen[dev].store((uint64_t)smem << 24 | (uint64_t)best_blocks << 12 | (uint64_t)best_block,
+      choice[dev].store((uint64_t)smem << 24 | (uint64_t)best_blocks << 12 | (uint64_t)best_block,
                         std::memory_order_relaxed);
   }
-  // no more blocks than there are rows (or row pieces) to cover: every block stages the table
-  const uint64_t work = p.ckpt_per_row ? p.R * p.ckpt_per_row : p.R;
-  const uint64_t need = (work + best_block - 1) / best_block;
+  // no more blocks than there are rows to cover: every block stages the table
+  const uint64_t need = (p.R + best_block - 1) / best_block;
   const int blocks = (int)std::min<uint64_t>((uint64_t)grid * best_blocks, std::max<uint64_t>(need, 1));
   kern<<<blocks, best_block, smem, stream>>>(p);
   return cudaGetLastError();
