@@ -115,6 +115,8 @@ struct SegRec {
 
 // Scratch bytes per row for recorded match positions (row-relative u32).
 constexpr uint32_t kRowSlotBytes = kRowSlots * 4;
+// Streaming emit pass: positions a lane collects in shared memory before the warp writes them.
+constexpr uint32_t kEmitBuf = 32;
 
 // Words of the ticket area (256 B at the start of a scan's header): the chunk ticket, the
 // counters of blocks that finished pass 1 and the emit pass, the streaming emit's ticket.

@@ -1609,6 +1609,9 @@ __global__ void __launch_bounds__(1024, 1)
   wc.bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
   wc.phase_bits = 0;
   wc.pending = 0;
+  // per lane kEmitBuf u16 positions (relative to the warp's base column), lane-major
+  uint16_t* const buf = reinterpret_cast<uint16_t*>(
+      sm + region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * (kLanes * kEmitBuf * 2)) + lane * kEmitBuf;
   if (lane == 0) {
     for (uint32_t b = 0; b < kStages; ++b) mbar_init(smem_u32(sm + wc.bar0 + 8 * b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1624,6 +1627,7 @@ __global__ void __launch_bounds__(1024, 1)
   const uint32_t A = p.dfa.first_accept;
   const uint32_t nblk = (uint32_t)(p.S / kBox);
   uint32_t* const tickets = p.ticket + kEmitTicketWord;
+  uint16_t* const wbuf = buf - lane * kEmitBuf;  // the warp's buffers
   bool failed = false;
   for (;;) {
     uint32_t ticket = 0;
@@ -1674,6 +1678,25 @@ __global__ void __launch_bounds__(1024, 1)
     const uint32_t b0 = fmin / kBox;
     const uint32_t b1 = min((lmax + kBox - 1) / kBox, nblk);
     const uint32_t in_row_end = min(lv, (uint32_t)p.S);
+    // Positions are collected per lane in shared memory and written by the whole warp one
+    // lane's run at a time (consecutive addresses, full sectors) instead of one scattered
+    // 8-byte store per position: flushed when a lane has no room for another vector's, or
+    // when the columns would no longer fit 16 bits above the warp's base column.
+    const uint64_t rowbase = p.pos_base + p.h + r * p.S;
+    uint32_t cnt = 0, base = b0 * kBox;
+    auto flush = [&]() {
+      __syncwarp();  // every lane's buffer writes are visible to the warp
+      for (uint32_t src = 0; src < kLanes; ++src) {
+        const uint32_t n = __shfl_sync(kFull, cnt, src);
+        if (n == 0) continue;
+        const uint64_t os = __shfl_sync(kFull, o, src);
+        const uint64_t vb = __shfl_sync(kFull, rowbase, src) + base;
+        if (lane < n) p.positions[os + lane] = vb + wbuf[src * kEmitBuf + lane];
+      }
+      __syncwarp();
+      o += cnt;
+      cnt = 0;
+    };
     if (b0 < b1) {
       const uint32_t nb = b1 - b0;
       const uint32_t first = nb < kStages ? nb : kStages;
@@ -1712,24 +1735,30 @@ __global__ void __launch_bounds__(1024, 1)
           wc.pending |= 1u << b;
         }
         const uint32_t col0 = (b0 + k) * kBox;
-        const uint64_t pb = p.pos_base + p.h + r * p.S + col0;
+        if (col0 + kBox - base > 0xFFFFu) {  // warp-uniform
+          flush();
+          base = col0;
+        }
 #pragma unroll
         for (uint32_t i = 0; i < kBox / 16; ++i) {
           const uint32_t col = col0 + i * 16u;
-          if (col >= fv && col + 16u <= in_row_end && o < end) {
+          if (col >= fv && col + 16u <= in_row_end && o + cnt < end) {
             uint32_t m = 0;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
               x = tab.next(x, tab.col(byte_of(v[i], q)));
               m |= (x >= A ? 1u : 0u) << q;
             }
-            while (m != 0 && o < end) {
-              p.positions[o++] = pb + i * 16u + (uint32_t)(__ffs(m) - 1);
+            const uint32_t rel = col - base;
+            while (m != 0 && o + cnt < end) {
+              buf[cnt++] = (uint16_t)(rel + (uint32_t)(__ffs(m) - 1));
               m &= m - 1u;
             }
           }
+          if (__any_sync(kFull, cnt > kEmitBuf - 16)) flush();
         }
       }
+      flush();
       if (failed) break;
     }
     // the last row's window past the last full row (its tail)
@@ -1948,7 +1977,7 @@ cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, in
   if (p.stream_emit && tm != nullptr) {
     // dense matches: pass 1's launch shape (one block per SM, warps as shared memory allows)
     auto kern = k_emit_stream<LAYOUT, ESIZE>;
-    const size_t per_warp = kStages * kStageBytes + kStages * 8;
+    const size_t per_warp = kStages * kStageBytes + kStages * 8 + kLanes * kEmitBuf * 2;
     const size_t fixed = smem + 1024;  // column map and table, then alignment of the stages
     int optin = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);

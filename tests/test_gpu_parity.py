@@ -308,7 +308,7 @@ def test_clustered_matches_after_a_sparse_scan(torch, offset, cap_div):
     dfa.free()
 
 
-@pytest.mark.parametrize("seg", [0, 4160, 8192])
+@pytest.mark.parametrize("seg", [0, 4160, 8192, 196608])
 def test_dense_emission(torch, seg):
     # dense matches (10 %, then a stretch where every byte matches): positions in order,
     # with and without capacity truncation
@@ -329,10 +329,10 @@ def test_dense_emission(torch, seg):
     o = pm.MatchOpts(segment_bytes=seg)
     want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
     assert want.match_count > (text.size >> 6) + (1 << 20)
-    # a fresh DFA emits row by row; once a scan of it has seen the density, pass 1
-    # writes a checkpoint every 2 KiB of each row and the emit pass works on the pieces in
-    # parallel (the first piece of a row starts at its merge point, the last row's tail
-    # belongs to its last piece)
+    # a fresh DFA emits row by row; once a scan of it has seen the density, the emit pass
+    # streams the rows through shared memory and writes each lane's positions warp-wide
+    # (rows of 192 KiB take the buffers' base column past 64 KiB; the last row's tail is
+    # replayed from global memory)
     for learn in (False, True):
         dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
         if learn:
