@@ -168,6 +168,37 @@ int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
                    const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
                    parem_dfa** out);
 
+/*
+ * Regular expressions (host only, no GPU): the operators of the paper's Table III --
+ * concatenation ab, Kleene star a*, union a|b, positive closure a+, range [0..9] (also
+ * written [0-9]; [^..] negates a set), optionality a?, group ( ) -- compiled by the
+ * McNaughton-Yamada-Thompson construction and the subset construction (Section IV) into a
+ * DFA for parem_load_dfa.  A byte stands for itself, '\' escapes the next one (\n \t \r
+ * \0 \xHH), '.' is any byte, and an empty alternative matches the empty string.  Bytes
+ * that every edge treats alike share one symbol, so the table has one column per class.
+ *
+ * flags: 0 = search: the DFA is in an accepting state after position j exactly when some
+ * suffix of text[0..j], possibly empty, matches (the DFA of Sigma* R), so parem_match counts
+ * and emits every such j; PAREM_REGEX_ANCHORED: when text[0..j] matches.
+ * max_states caps the DFA (0: 65,535).  The DFA state 0 is the start; table entries are
+ * PAREM_NONE where no match can continue.
+ * Errors: INVALID_ARG (null pointer, unknown flag, syntax error), TOO_LARGE (more states
+ * than max_states, or a pattern longer than 16 KiB), OOM.
+ */
+#define PAREM_REGEX_ANCHORED 1u
+typedef struct parem_regex parem_regex;
+int parem_regex_compile(const char* pattern, uint64_t len, uint32_t flags, uint32_t max_states,
+                        parem_regex** out);
+/* The DFA's size: states and symbols (byte classes). */
+int parem_regex_info(const parem_regex* re, uint32_t* n_states, uint32_t* n_symbols);
+/* The DFA in parem_load_dfa's form: table (n_states * n_symbols, row-major), the 256-entry
+ * byte-to-symbol map, accept flags (n_states) and the start state; caller-owned buffers. */
+int parem_regex_export(const parem_regex* re, uint32_t* table, uint16_t* byte_to_symbol, uint8_t* accept,
+                       uint32_t* start);
+/* parem_load_dfa of the compiled DFA. */
+int parem_regex_load(const parem_regex* re, parem_dfa** out);
+void parem_regex_free(parem_regex* re);
+
 /* Host-only preparation of the same inputs, without touching the GPU: validates them and
  * fills *info.  Errors: INVALID_ARG. */
 int parem_prepare_info(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,

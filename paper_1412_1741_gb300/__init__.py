@@ -28,7 +28,8 @@ __all__ = [
     "parem_version", "parem_last_stats", "parem_match_noalloc", "Stats", "EXPORTED_SYMBOLS",
     "PAREM_ERR_TOO_LARGE", "PAREM_NOALLOC_SCRATCH_BYTES", "parem_batch_create", "Batch", "BatchOpts",
     "parem_server_create", "Server", "ServerOpts", "make_requests", "parem_clock_ns", "REQUEST_DTYPE",
-    "RESPONSE_DTYPE", "PAREM_SERVE_BATCH", "PAREM_SERVE_FIFO",
+    "RESPONSE_DTYPE", "PAREM_SERVE_BATCH", "PAREM_SERVE_FIFO", "PAREM_REGEX_ANCHORED", "RegexDfa",
+    "parem_regex_compile", "parem_load_regex",
 ]
 
 PAREM_NONE = 0xFFFFFFFF
@@ -48,7 +49,8 @@ EXPORTED_SYMBOLS = [
     "parem_last_stats", "parem_match_noalloc", "parem_batch_create", "parem_batch_run", "parem_batch_results",
     "parem_batch_item_segment", "parem_batch_stats", "parem_batch_free", "parem_server_create", "parem_server_submit",
     "parem_server_poll", "parem_server_drain", "parem_server_replay", "parem_server_get_stats",
-    "parem_server_free", "parem_clock_ns",
+    "parem_server_free", "parem_clock_ns", "parem_regex_compile", "parem_regex_info", "parem_regex_export",
+    "parem_regex_load", "parem_regex_free",
 ]
 
 
@@ -159,8 +161,15 @@ def load_library(build_if_missing: bool = False):
     lib.parem_strerror.argtypes = [ctypes.c_int]
     lib.parem_strerror.restype = ctypes.c_char_p
     lib.parem_version.restype = ctypes.c_char_p
+    lib.parem_regex_compile.argtypes = [ctypes.c_char_p, u64, u32, u32, ctypes.POINTER(vp)]
+    lib.parem_regex_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.parem_regex_export.argtypes = [vp, vp, vp, vp, ctypes.POINTER(u32)]
+    lib.parem_regex_load.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.parem_regex_free.argtypes = [vp]
+    lib.parem_regex_free.restype = None
     for f in ("parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_match", "parem_match_ex",
-              "parem_match_host", "parem_release_scratch", "parem_last_stats", "parem_match_noalloc"):
+              "parem_match_host", "parem_release_scratch", "parem_last_stats", "parem_match_noalloc",
+              "parem_regex_compile", "parem_regex_info", "parem_regex_export", "parem_regex_load"):
         getattr(lib, f).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -237,6 +246,51 @@ def parem_load_dfa(table, byte_to_symbol, start, accept) -> Dfa:
     info = _Info()
     lib.parem_dfa_get_info(h, ctypes.byref(info))
     return Dfa(h, _info(info))
+
+
+PAREM_REGEX_ANCHORED = 1
+
+
+@dataclass
+class RegexDfa:
+    """A compiled regular expression: the DFA in parem_load_dfa's form (host arrays)."""
+    table: np.ndarray           # (n_states, n_symbols) uint32, PAREM_NONE where no match continues
+    byte_to_symbol: np.ndarray  # (256,) uint16
+    accept: np.ndarray          # (n_states,) uint8
+    start: int
+
+
+def parem_regex_compile(pattern, flags: int = 0, max_states: int = 0) -> RegexDfa:
+    """Compile a regular expression (bytes or str) with the operators of Table III into a
+    DFA (host only).  flags 0: search (accept after every position where a match ends);
+    PAREM_REGEX_ANCHORED: prefixes."""
+    lib = load_library()
+    pat = pattern.encode() if isinstance(pattern, str) else bytes(pattern)
+    h = ctypes.c_void_p()
+    rc = lib.parem_regex_compile(pat, len(pat), int(flags), int(max_states), ctypes.byref(h))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_regex_compile")
+    try:
+        ns, nsym = ctypes.c_uint32(), ctypes.c_uint32()
+        rc = lib.parem_regex_info(h, ctypes.byref(ns), ctypes.byref(nsym))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_regex_info")
+        table = np.empty((ns.value, nsym.value), np.uint32)
+        b2s = np.empty(256, np.uint16)
+        acc = np.empty(ns.value, np.uint8)
+        start = ctypes.c_uint32()
+        rc = lib.parem_regex_export(h, table.ctypes.data, b2s.ctypes.data, acc.ctypes.data, ctypes.byref(start))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_regex_export")
+    finally:
+        lib.parem_regex_free(h)
+    return RegexDfa(table, b2s, acc, int(start.value))
+
+
+def parem_load_regex(pattern, flags: int = 0, max_states: int = 0) -> Dfa:
+    """Compile a regular expression and load its DFA on the current device."""
+    r = parem_regex_compile(pattern, flags, max_states)
+    return parem_load_dfa(r.table, r.byte_to_symbol, r.start, r.accept)
 
 
 def parem_dfa_get_info(dfa: Dfa) -> DfaInfo:

@@ -425,3 +425,17 @@ def test_enumeration_mode_with_bitmap(torch):
     spec = wl.DfaSpec(t, 0, acc, None, "rand600x8")
     text = wl.uniform_text(200_000, 8, seed=10)
     check(torch, spec, text, opts=pm.MatchOpts(enumerate_all=1, segment_bytes=2048))
+
+
+@pytest.mark.parametrize("pattern,anchored", [("(a|b)?c*[0..3]b+", False), ("(ab|c)*d", True),
+                                               ("x[^ab]y|[0..9]+\\.[0..9]", False),
+                                               ("(a|b)*a(a|b)(a|b)(a|b)(a|b)", False)])
+def test_regex_dfa_scan(torch, pattern, anchored):
+    # a DFA compiled from a regular expression (Table III operators) scanned on the GPU
+    # equals the oracle's run of the same DFA (layouts and speculation as for any DFA)
+    r = pm.parem_regex_compile(pattern, pm.PAREM_REGEX_ANCHORED if anchored else 0)
+    spec = wl.DfaSpec(r.table, r.start, r.accept, r.byte_to_symbol, f"re:{pattern}")
+    rng = np.random.default_rng(len(pattern))
+    text = rng.choice(np.frombuffer(b"abcdxy0123.", np.uint8), size=(3 << 20) + 77)
+    check(torch, spec, text, offset=3)
+    check(torch, spec, text[:50_001], opts=pm.MatchOpts(segment_bytes=256))
