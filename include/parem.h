@@ -54,7 +54,7 @@ extern "C" {
 #define PAREM_ERR_TIMEOUT (-4)     /* a bounded device-side wait ran out */
 #define PAREM_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define PAREM_ERR_INTERNAL (-6)    /* a device-side self-check failed */
-#define PAREM_ERR_UNSUPPORTED (-7) /* valid request outside what this build supports */
+#define PAREM_ERR_UNSUPPORTED (-7) /* valid request outside what the library supports */
 #define PAREM_ERR_TOO_LARGE (-8)   /* parem_match_noalloc: the request needs more scratch than
                                       its fixed area (PAREM_NOALLOC_SCRATCH_BYTES) holds */
 
