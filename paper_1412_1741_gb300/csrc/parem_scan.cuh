@@ -1574,8 +1574,19 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;
   const DeviceDfa& D = p.dfa;
-  load_tables<LAYOUT, ESIZE>(sm, D);
-  __syncthreads();
+  // The table is staged only by blocks with a row to replay: rows whose matches pass 1
+  // recorded are copied (sparse texts: nearly all of them), so most blocks never read it.
+  bool replay = false;
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    const SegRec& sr = p.segrec[r];
+    replay = replay || (sr.count > 0 && sr.offset < p.capacity &&
+                        ((sr.flags & (kHeadFlag | kPreFlag)) || (!(sr.flags & kSlotsFlag) && sr.lv > 0)));
+  }
+  if (__syncthreads_or(replay)) {
+    load_tables<LAYOUT, ESIZE>(sm, D);
+    __syncthreads();
+  }
   Tab<LAYOUT, ESIZE> tab;
   tab.sm = sm;
   tab.gtable = D.table;
