@@ -258,6 +258,13 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
   D.max_cand = P.max_cand;
   D.stride_k = P.stride_k;
   D.stride_off = P.stride_off;
+  {
+    const uint32_t K = P.stride_k;
+    D.stride_k4 = K * K * K * K;
+    D.stride_wts = K <= 6 ? (K * K * K | (K * K) << 8 | K << 16 | 1u << 24) : 0u;
+    D.stride_krep = K * 0x01010101u;
+    D.stride_kmrep = K ? (K - 1) * 0x01010101u : 0u;
+  }
   D.win = P.win;
   fill_info(P, &d->info);
   *out = d;

@@ -96,6 +96,10 @@ struct DeviceDfa {
   uint32_t n, n_classes, first_accept, dead, start;
   uint32_t layout, esize, rowbytes, table_bytes, max_cand;
   uint32_t stride_k, stride_off;  // kByteStride (see Prepared)
+  // kByteStride constants of the main run, computed on the host so that the loop reads them
+  // as kernel-parameter operands: K^4, the byte dot-product weights (K^3, K^2, K, 1) for
+  // K <= 6, and K and K - 1 in every byte
+  uint32_t stride_k4, stride_wts, stride_krep, stride_kmrep;
   uint32_t win;                   // kClassWin (see Prepared)
 };
 

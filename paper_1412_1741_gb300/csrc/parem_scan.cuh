@@ -997,22 +997,20 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           if constexpr (LAYOUT == kByteStride) {
             // four bytes per lookup: the stride table holds the state after them and how
             // many of the four steps end in an accepting state
-            const uint32_t K = D.stride_k, km = K - 1, k4 = K * K * K * K;
+            const uint32_t K = D.stride_k, km = K - 1, k4 = D.stride_k4;
             const uint8_t* stab = sm + kTableOff + D.stride_off;
             const uint32_t ws[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
-            if (K <= 6) {
-              // the four symbols of a word at once: clamp every byte to K - 1 (bit 7 of
-              // (b | 0x80) - K is set when b & 0x7F >= K; bytes >= 128 clamp too), then the
-              // mixed-radix index m0 K^3 + m1 K^2 + m2 K + m3 as one byte dot product
-              const uint32_t ones = 0x01010101u, kmrep = km * ones;
-              const uint32_t wts = K * K * K | (K * K) << 8 | K << 16 | 1u << 24;
+            if (D.stride_wts != 0) {
+              // the four symbols of a word at once (K <= 6): clamp every byte to K - 1 (bit 7
+              // of (b | 0x80) - K is set when b & 0x7F >= K; bytes >= 128 clamp too), then
+              // the mixed-radix index m0 K^3 + m1 K^2 + m2 K + m3 as one byte dot product
 #pragma unroll
               for (int g = 0; g < 4; ++g) {
                 const uint32_t w = ws[g];
-                const uint32_t over = (((w | 0x80808080u) - K * ones) | w) & 0x80808080u;
+                const uint32_t over = (((w | 0x80808080u) - D.stride_krep) | w) & 0x80808080u;
                 const uint32_t mask = (over >> 7) * 0xFFu;
-                const uint32_t m = (w & ~mask) | (kmrep & mask);
-                const uint32_t e = stab[__dp4a(m, wts, s * k4)];
+                const uint32_t m = (w & ~mask) | (D.stride_kmrep & mask);
+                const uint32_t e = stab[__dp4a(m, D.stride_wts, s * k4)];
                 s = e & 31u;
                 mu += e >> 5;
               }
