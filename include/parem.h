@@ -173,7 +173,7 @@ int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
  * concatenation ab, Kleene star a*, union a|b, positive closure a+, range [0..9] (also
  * written [0-9]; [^..] negates a set), optionality a?, group ( ) -- compiled by the
  * McNaughton-Yamada-Thompson construction and the subset construction (Section IV) into a
- * DFA for parem_load_dfa.  A byte stands for itself, '\' escapes the next one (\n \t \r
+ * DFA for parem_load_dfa, which is then minimized.  A byte stands for itself, '\' escapes the next one (\n \t \r
  * \0 \xHH), '.' is any byte, and an empty alternative matches the empty string.  Bytes
  * that every edge treats alike share one symbol, so the table has one column per class.
  *

@@ -8,9 +8,10 @@
 // McNaughton-Yamada-Thompson construction (one fragment per node, joined by empty
 // transitions); the subset construction turns the NFA into a DFA.  Bytes that every NFA
 // edge treats alike share one DFA symbol (byte classes), so the table has one column per
-// class.  For a search (the default) the NFA's start state also loops on every byte, so the
-// DFA accepts after position j exactly when some suffix of text[0..j], possibly empty,
-// matches (Sigma* R); anchored compilation accepts when text[0..j] matches.
+// class; the DFA is then minimized (Moore's partition refinement).  For a search (the
+// default) the NFA's start state also loops on every byte, so the DFA accepts after
+// position j exactly when some suffix of text[0..j], possibly empty, matches (Sigma* R);
+// anchored compilation accepts when text[0..j] matches.
 //
 // Syntax: a byte stands for itself; '\' escapes the next byte (\n \t \r \0 \xHH as usual);
 // '.' is any byte; [..] is a set of bytes and ranges, written a-z or (as in the paper)
@@ -238,6 +239,59 @@ struct Nfa {
   }
 };
 
+// Moore's partition refinement: the minimal DFA of the same language.  The empty subset
+// (no match can continue: table entry PAREM_NONE) is an explicit dead state during the
+// refinement and PAREM_NONE again afterwards; the start state keeps number 0.
+void minimize(uint32_t& n, uint32_t k, std::vector<uint32_t>& table, std::vector<uint8_t>& accept) {
+  const uint32_t dead = n;  // extra state: every transition to itself, not accepting
+  auto next = [&](uint32_t q, uint32_t c) -> uint32_t {
+    if (q == dead) return dead;
+    const uint32_t t = table[(uint64_t)q * k + c];
+    return t == PAREM_NONE ? dead : t;
+  };
+  std::vector<uint32_t> cls(n + 1);
+  for (uint32_t q = 0; q < n; ++q) cls[q] = accept[q] ? 1u : 0u;
+  cls[dead] = 0;
+  uint32_t n_cls = 0;
+  for (;;) {
+    std::map<std::vector<uint32_t>, uint32_t> id;
+    std::vector<uint32_t> nc(n + 1);
+    std::vector<uint32_t> sig(k + 1);
+    for (uint32_t q = 0; q <= n; ++q) {
+      sig[0] = cls[q];
+      for (uint32_t c = 0; c < k; ++c) sig[c + 1] = cls[next(q, c)];
+      nc[q] = id.emplace(sig, (uint32_t)id.size()).first->second;
+    }
+    const uint32_t m = (uint32_t)id.size();
+    cls.swap(nc);
+    if (m == n_cls) break;
+    n_cls = m;
+  }
+  // new numbering: the start's class first, the dead class dropped
+  const uint32_t dead_cls = cls[dead];
+  std::vector<uint32_t> renum(n_cls, PAREM_NONE);
+  uint32_t m = 0;
+  renum[cls[0]] = m++;
+  for (uint32_t q = 0; q < n; ++q)
+    if (cls[q] != dead_cls && renum[cls[q]] == PAREM_NONE) renum[cls[q]] = m++;
+  std::vector<uint32_t> t2((uint64_t)m * k, PAREM_NONE);
+  std::vector<uint8_t> a2(m, 0);
+  std::vector<char> done(m, 0);
+  for (uint32_t q = 0; q < n; ++q) {
+    const uint32_t r = renum[cls[q]];
+    if (r == PAREM_NONE || done[r]) continue;
+    done[r] = 1;
+    a2[r] = accept[q];
+    for (uint32_t c = 0; c < k; ++c) {
+      const uint32_t t = next(q, c);
+      t2[(uint64_t)r * k + c] = (t == dead || cls[t] == dead_cls) ? PAREM_NONE : renum[cls[t]];
+    }
+  }
+  n = m;
+  table.swap(t2);
+  accept.swap(a2);
+}
+
 }  // namespace
 
 struct parem_regex {
@@ -352,6 +406,9 @@ extern "C" int parem_regex_compile(const char* pattern, uint64_t len, uint32_t f
     for (int x : subsets[q])
       if (x == accept_state) re->accept[q] = 1;
   }
+  // the subset construction can leave equivalent states (e.g. the start subset of a search);
+  // the scan prefers the minimal DFA: fewer states, fewer speculation candidates
+  minimize(re->n_states, re->n_symbols, re->table, re->accept);
   *out = re;
   return PAREM_OK;
 }

@@ -107,7 +107,21 @@ def test_state_limit():
         pm.parem_regex_compile(pattern, max_states=256)
     assert e.value.status == pm.PAREM_ERR_TOO_LARGE
     r = pm.parem_regex_compile(pattern, max_states=4096)
-    assert r.table.shape[0] >= 1024
+    assert r.table.shape[0] == 1024  # minimal
     rng = np.random.default_rng(3)
     text = bytes(rng.choice(np.frombuffer(b"ab", np.uint8), size=60))
     assert np.array_equal(dfa_positions(r, text), brute_force(pattern, text, False))
+
+
+@pytest.mark.parametrize("pattern,anchored,states", [
+    ("a*", False, 1),            # every suffix matches (the empty one): one accepting state
+    ("(a|b)*", True, 1),         # the empty prefix matches too: one accepting state (others: dead)
+    ("a|aa|aaa", True, 4),       # a, aa, aaa: the start and three accepting states
+    ("(ab|ab)c", True, 4),       # the duplicate alternative collapses
+    ("x*y", False, 2),
+])
+def test_minimal_dfa_sizes(pattern, anchored, states):
+    # the compiled DFA is minimal: its state count is the Myhill-Nerode index of the language
+    # (the dead state is implicit, as PAREM_NONE entries)
+    r = pm.parem_regex_compile(pattern, pm.PAREM_REGEX_ANCHORED if anchored else 0)
+    assert r.table.shape[0] == states, r.table
