@@ -23,8 +23,9 @@ def lib():
 
 
 def to_python(pattern: str) -> str:
-    """The same expression in Python's syntax: the paper's ranges a..z become a-z."""
-    return re.sub(r"(\\?.)\.\.(\\?.)", r"\1-\2", pattern)
+    """The same expression in Python's syntax: inside [...] sets the paper's ranges a..z
+    become a-z (outside a set, '..' is two any-byte atoms and stays)."""
+    return re.sub(r"\[[^\]]*\]", lambda m: re.sub(r"(\\?.)\.\.(\\?.)", r"\1-\2", m.group(0)), pattern)
 
 
 def brute_force(pattern: str, text: bytes, anchored: bool) -> np.ndarray:
@@ -125,3 +126,35 @@ def test_minimal_dfa_sizes(pattern, anchored, states):
     # (the dead state is implicit, as PAREM_NONE entries)
     r = pm.parem_regex_compile(pattern, pm.PAREM_REGEX_ANCHORED if anchored else 0)
     assert r.table.shape[0] == states, r.table
+
+
+def random_pattern(rng, depth=0):
+    """A random expression over a small alphabet from Table III's operators."""
+    r = rng.random()
+    if depth >= 3 or r < 0.3:
+        kind = rng.integers(4)
+        if kind == 0:
+            return str(rng.choice(list("abc")))
+        if kind == 1:
+            lo, hi = sorted(rng.choice(list("abcd"), size=2))
+            return f"[{lo}..{hi}]"
+        if kind == 2:
+            return "[^" + str(rng.choice(list("abc"))) + "]"
+        return "."
+    if r < 0.55:
+        return random_pattern(rng, depth + 1) + random_pattern(rng, depth + 1)
+    if r < 0.7:
+        return "(" + random_pattern(rng, depth + 1) + "|" + random_pattern(rng, depth + 1) + ")"
+    return "(" + random_pattern(rng, depth + 1) + ")" + str(rng.choice(list("*+?")))
+
+
+def test_random_expressions_match_re_brute_force():
+    # 200 random expressions of nested operators, each on random texts, search and anchored
+    rng = np.random.default_rng(2024)
+    alphabet = np.frombuffer(b"abcdx", np.uint8)
+    for _ in range(200):
+        pattern = random_pattern(rng)
+        for anchored in (False, True):
+            r = pm.parem_regex_compile(pattern, pm.PAREM_REGEX_ANCHORED if anchored else 0)
+            text = bytes(rng.choice(alphabet, size=int(rng.integers(0, 30))))
+            assert np.array_equal(dfa_positions(r, text), brute_force(pattern, text, anchored)), (pattern, text)
