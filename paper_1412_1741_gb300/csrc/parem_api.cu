@@ -665,6 +665,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
 extern "C" int parem_match_ex(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                               uint64_t capacity, const parem_match_opts* opts, void* stream, parem_result* out) {
   if (!dfa || !out || (len > 0 && !text) || len > kMaxText) return PAREM_ERR_INVALID_ARG;
+  NvtxRange range("parem_match");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
   if (dev != dfa->device) return PAREM_ERR_INVALID_ARG;
@@ -679,6 +680,7 @@ extern "C" int parem_match(const parem_dfa* dfa, const uint8_t* text, uint64_t l
 extern "C" int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                                 uint64_t capacity, void* stream, parem_result* out) {
   if (!dfa || !out || (len > 0 && !text) || len > kMaxText) return PAREM_ERR_INVALID_ARG;
+  NvtxRange range("parem_match_host");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
   if (dev != dfa->device) return PAREM_ERR_INVALID_ARG;

@@ -667,6 +667,7 @@ extern "C" int parem_batch_create(const parem_batch_item* items, uint32_t n_item
 
 extern "C" int parem_batch_run(parem_batch* batch, void* stream) {
   if (!batch) return PAREM_ERR_INVALID_ARG;
+  NvtxRange range("parem_batch_run");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAREM_ERR_CUDA;
   if (dev != batch->device) return PAREM_ERR_INVALID_ARG;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 
@@ -29,6 +30,15 @@ struct parem_dfa {
 };
 
 namespace parem {
+
+// A named range on the host timeline of profilers that read NVTX (one per API call); without
+// a profiler attached the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 // Shortest row length worth speculating for this DFA: a multiple of its learned convergence
 // length, or for DFAs whose candidate sets are large relative to their states (random-like
 // automata, which need about twice their state count to synchronise) a multiple of n.

@@ -126,6 +126,7 @@ parem_response make_response(const Req& q, int status, uint32_t batch_size, cons
 // Plan and launch one batch into arena `ai`.  Requests that do not fit go back to the head of
 // the queue; a single request that does not fit an empty arena is answered TOO_LARGE.
 void launch_round(parem_server* s, int ai, std::vector<Req>& take, std::unique_lock<std::mutex>& lk) {
+  NvtxRange range("parem_server launch");
   Arena& A = s->arenas[ai];
   for (;;) {
     std::vector<parem_batch_item> items(take.size());
