@@ -1,7 +1,7 @@
 """Reference oracle for PaREM DFA matching.  TEST INFRASTRUCTURE ONLY.
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
-import this module.  The product package never imports it, and it imports nothing from the
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py`` (the
+``cpu_baseline`` of a bench line and the ``--impl reference`` arm) may import this module.  The product package never imports it, and it imports nothing from the
 product package: the two share no code, tables or helpers.
 
 Contents

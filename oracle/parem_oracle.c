@@ -1,8 +1,8 @@
 /*
  * parem_oracle.c -- the reference oracle for DFA matching.  TEST INFRASTRUCTURE ONLY.
  *
- * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load this
- * library.  The product path (libparem) never links, loads or calls it, and it shares no
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU legs (the cpu_baseline of a bench
+ * line and the --impl reference arm) may load this library.  The product path (libparem) never links, loads or calls it, and it shares no
  * header, table or helper with the CUDA path.
  *
  * What it computes is the plain definition of running a DFA (Q, Sigma, delta, q0, F) over a
