@@ -237,40 +237,80 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(spec, text_dev, budget_s=12.0):
-    """Time the oracle on the host on a bounded sample (whole passes over a prefix)."""
+def cpu_baseline_and_parity(spec, text_dev, got, pos_dev):
+    """The oracle over the WHOLE text (copied to the host): the time of its pass that writes
+    the positions is the CPU baseline (one thread: the sequential run does not split), and
+    its result is compared with the GPU's last timed call -- final state, acceptance, match
+    count and every position written.  Returns (cpu_baseline, parity)."""
     import numpy as np
 
     from oracle import oracle
 
     oracle.build()
     n = int(text_dev.numel())
-    probe = min(n, 64 << 20)
-    host = text_dev[:probe].cpu().numpy()
-    t0 = time.perf_counter()
-    oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, host, want_positions=False)
-    rate = probe / max(time.perf_counter() - t0, 1e-6)
-    sample = int(min(n, max(probe, rate * budget_s)))
-    host = text_dev[:sample].cpu().numpy() if sample > probe else host
-    host = np.ascontiguousarray(host)
-    t0 = time.perf_counter()
-    r = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, host, want_positions=True)
-    dt = time.perf_counter() - t0
-    return {"value": round(sample / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample / (1 << 20):.0f} MiB of the text, one single-threaded pass "
-                      f"({r.match_count} matches, {dt:.1f} s)"}
+    host = np.ascontiguousarray(text_dev.cpu().numpy())
+    times = []
+    want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, host,
+                       want_positions=pos_dev is not None, times=times)
+    dt = times[-1]
+    checks = {"final_state": int(got.final_state) == int(want.final_state),
+              "accepted": bool(got.accepted) == bool(want.accepted),
+              "match_count": int(got.match_count) == int(want.match_count)}
+    if pos_dev is not None:
+        k = int(got.n_written)
+        g = pos_dev[:k].cpu().numpy().view(np.uint64)
+        checks["positions"] = bool(k == min(int(pos_dev.numel()), want.match_count) and
+                                   np.array_equal(g, want.positions[:k]))
+    ok = all(checks.values())
+    parity = {"ok": ok, "checked": "whole text" + (", every position" if pos_dev is not None else ", count only"),
+              "text_bytes": n, "oracle_matches": int(want.match_count), "gpu_matches": int(got.match_count),
+              "oracle_final_state": int(want.final_state), "gpu_final_state": int(got.final_state), **checks}
+    cpu = {"value": round(n / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"the whole {n / (1 << 30):.2f} GiB text, one single-threaded pass of the C oracle writing "
+                     f"its {want.match_count} positions ({dt:.1f} s; a counting pass before it sizes the buffer)"}
+    return cpu, parity
 
 
-def run_batch(args, rank, world, local_rank):
-    """Batched configuration: one graph launch per step over all texts vs a loop of plain calls."""
-    import numpy as np
+def oracle_all_cores(jobs):
+    """Run independent oracle scans on all host cores (ctypes releases the GIL, so threads run
+    the C loops in parallel).  jobs: list of (spec, host_text, start).  Returns (results,
+    seconds, threads)."""
+    import concurrent.futures as cf
+
+    from oracle import oracle
+
+    oracle.build()
+    if jobs:  # load the library once before the threads start
+        oracle.scan(jobs[0][0].table, jobs[0][0].byte_to_symbol, jobs[0][2], jobs[0][0].accept, jobs[0][1][:1],
+                    want_positions=False)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        res = list(ex.map(lambda j: oracle.scan(j[0].table, j[0].byte_to_symbol, j[2], j[0].accept, j[1],
+                                                want_positions=False), jobs))
+    return res, time.perf_counter() - t0, threads
+
+
+def host_link_gbs(host_pinned, dev_buf):
+    """Host-to-device copy rate of a pinned buffer (GB/s, 1e9): what bounds the end-to-end
+    path with host buffers."""
     import torch
 
-    import __graft_entry__ as ge
-    import paper_1412_1741_gb300 as pm
-    from paper_1412_1741_gb300 import workloads as wl
+    stream = torch.cuda.current_stream()
+    dev_buf.copy_(host_pinned, non_blocking=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        dev_buf.copy_(host_pinned, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return 3 * host_pinned.numel() / (a.elapsed_time(b) / 1e3) / 1e9
 
-    ge.build()
+
+def setup_rank(local_rank, world):
+    import torch
+
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     dist = None
@@ -278,6 +318,19 @@ def run_batch(args, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+    return dev, dist
+
+
+def batch_measure(args, rank, world, dev, dist):
+    """Batched configuration: one graph launch per step over all texts (count only) vs a loop
+    of plain calls on the same texts; every item's result is compared with the oracle, run
+    over all texts on all host cores (its time is the CPU baseline).  Returns the line."""
+    import numpy as np
+    import torch
+
+    import paper_1412_1741_gb300 as pm
+    from paper_1412_1741_gb300 import workloads as wl
+
     n_texts = args.batch_texts
     specs = wl.batch_dfas(32, seed=6)
     lengths = wl.batch_lengths(n_texts, seed=6 + rank)
@@ -293,7 +346,7 @@ def run_batch(args, rank, world, local_rank):
     for _ in range(args.warmup):
         batch.run()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index)
     clocks.start()
     if dist:
         dist.barrier()
@@ -311,11 +364,11 @@ def run_batch(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = ev0.elapsed_time(ev1)
-    total_ms = max_over_ranks(total_ms, dist, dev)
+    total_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     step_ms = sorted(a.elapsed_time(b) for a, b in evs)
     res = batch.results()
-    # plain: one parem_match per text on the same stream (same texts, same results)
+    segs = batch.segments()
+    # plain: one parem_match per text on the same stream (same texts)
     for i in range(min(64, n_texts)):
         pm.parem_match(items[i][0], items[i][1], length=items[i][2])
     torch.cuda.synchronize()
@@ -324,56 +377,64 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
     agree = all((a.final_state, a.match_count) == (b.final_state, b.match_count) for a, b in zip(res, plain))
-    if rank != 0:
-        if dist:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-    value = job_gbs(total, world, args.steps, total_ms)
-    peak, peak_kind = measured_peaks()
-    achieved = total / (step_ms[len(step_ms) // 2] / 1e3) / 1e9
-    segs = batch.segments()
-    line = {
-        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": CONFIGS["d4"]["workload"], "texts": n_texts, "text_bytes": total, "dfas": len(dfas),
-                   "positions": "count only", "plan_seconds_with_autotune": round(plan_s, 3),
-                   "segment_bytes_median": int(np.median([s for s in segs if s] or [0])),
-                   "l2": "inputs larger than L2 (7.27 GB)", "parallelism": f"replicas x{world}"},
-        "p50_ms": round(step_ms[len(step_ms) // 2], 4),
-        "p99_ms": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
-        "batched_vs_plain": {"batched_gbs": round(value, 2), "plain_gbs": round(total / plain_s / 1e9, 2),
-                             "speedup": round(value / world / (total / plain_s / 1e9), 2),
-                             "plain_calls": n_texts, "results_agree": agree},
-        "roofline": {"bound": "hbm", "kernel": "whole batch graph (k_batch_scan + tiny kernel + copies)",
-                     "achieved": round(achieved, 1), "peak": peak,
-                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None},
-        "gpu_launches": args.steps * 2,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
     batch.free()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    line = None
+    if rank == 0:
+        # the oracle on every text, all host cores; parity of every item
+        host = arena.cpu().numpy()
+        jobs = [(specs[i % len(specs)], host[int(offs[i]):int(offs[i]) + int(lengths[i])], specs[i % len(specs)].start)
+                for i in range(n_texts)]
+        want, cpu_s, threads = oracle_all_cores(jobs)
+        bad = [i for i, (g, w) in enumerate(zip(res, want))
+               if (int(g.final_state), int(g.match_count)) != (int(w.final_state), int(w.match_count))]
+        del host
+        value = job_gbs(total, world, args.steps, total_ms)
+        plain_gbs = total / plain_s / 1e9
+        peak, peak_kind = measured_peaks()
+        achieved = total / (step_ms[len(step_ms) // 2] / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": CONFIGS["d4"]["workload"], "texts": n_texts, "text_bytes": total, "dfas": len(dfas),
+                       "positions": "count only", "plan_seconds_with_autotune": round(plan_s, 3),
+                       "segment_bytes_median": int(np.median([x for x in segs if x] or [0])),
+                       "l2": "inputs larger than L2 (7.27 GB)", "parallelism": f"replicas x{world}"},
+            "p50_ms": round(step_ms[len(step_ms) // 2], 4),
+            "p99_ms": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
+            "batched_vs_plain": {"batched_gbs": round(value / world, 2), "plain_gbs": round(plain_gbs, 2),
+                                 "speedup": round(value / world / plain_gbs, 2), "plain_calls": n_texts,
+                                 "results_agree": agree},
+            "parity": {"ok": not bad, "checked": f"all {n_texts} items: final state and match count vs the oracle",
+                       "mismatched_items": bad[:8]},
+            "cpu_baseline": {"value": round(total / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "sample": f"all {n_texts} texts ({total / 1e9:.2f} GB), independent oracle scans on "
+                                       f"{threads} host threads ({cpu_s:.1f} s)"},
+            "roofline": {"bound": "hbm", "kernel": "whole batch graph (k_batch_scan + tiny kernel + copies)",
+                         "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)", "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None},
+            "gpu_launches": args.steps * 2,
+            "clocks": clk,
+        }
+    for d in dfas:
+        d.free()
+    del arena
+    torch.cuda.empty_cache()
+    return line
 
 
-def run_serve(args, rank, world, local_rank):
+def serve_measure(args, rank, world, dev):
     """Serving configuration: open-loop replay of a Poisson trace through the request server
-    (continuous batching), the same trace's head through the FIFO plain server, and a
-    saturation sweep over arrival rates."""
+    (continuous batching), the same trace's head through the FIFO plain server, a saturation
+    sweep over arrival rates, and the oracle (all host cores) on a bounded sample of the
+    trace's requests, whose responses it checks.  Returns the line."""
     import numpy as np
     import torch
 
-    import __graft_entry__ as ge
     import paper_1412_1741_gb300 as pm
     from paper_1412_1741_gb300 import workloads as wl
 
-    ge.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
     specs = wl.serve_dfas(128, seed=7)
     dfas = [pm.parem_load_dfa(s.table, s.byte_to_symbol, s.start, s.accept) for s in specs]
     pools = wl.serve_pools_device(dev, pool_bytes=1536 << 20, seed=7 + rank)
@@ -399,7 +460,7 @@ def run_serve(args, rank, world, local_rank):
     for w in range(args.warmup):
         srv.replay(trace(20000, 0.2, 100 + w))
     k0 = srv.stats()["kernels"]
-    clocks = ClockSampler(local_rank)
+    clocks = ClockSampler(dev.index)
     clocks.start()
     duration = float(args.serve_seconds)
     req = trace(20000, duration, 7 + rank)
@@ -427,7 +488,27 @@ def run_serve(args, rank, world, local_rank):
     agree = bool(np.array_equal(fresp["final_state"], resp["final_state"][: len(head)]) and
                  np.array_equal(fresp["match_count"], resp["match_count"][: len(head)]))
     best = max(sweep, key=lambda x: x["gbs"])
+    line = None
     if rank == 0:
+        # the oracle on the first requests of the trace, all host cores, against the responses
+        keys = [(sp.meta["family"], sp.meta["alphabet"]) for sp in specs]
+        host = {k: v.cpu().numpy() for k, v in pools.items()}
+        base = {k: v.data_ptr() for k, v in pools.items()}
+        budget, jobs = args.serve_oracle_gb * 1e9, []
+        for i in range(len(req)):
+            k = keys[int(req["dfa_index"][i])]
+            o = int(req["text"][i]) - base[k]
+            jobs.append((specs[int(req["dfa_index"][i])], host[k][o:o + int(req["len"][i])],
+                         specs[int(req["dfa_index"][i])].start))
+            budget -= int(req["len"][i])
+            if budget <= 0:
+                break
+        want, cpu_s, threads = oracle_all_cores(jobs)
+        nb = sum(int(j[1].size) for j in jobs)
+        bad = [i for i, w in enumerate(want)
+               if (int(resp["final_state"][i]), int(resp["match_count"][i]), int(resp["status"][i])) !=
+               (int(w.final_state), int(w.match_count), 0)]
+        del host
         line = {
             "metric": METRIC, "value": main["gbs"], "unit": "GB/s", "n_gpus": world, "steps": 1,
             "warmup": args.warmup, "ms_per_step": round(main["span_s"] * 1e3, 1), "higher_is_better": True,
@@ -441,6 +522,12 @@ def run_serve(args, rank, world, local_rank):
                         "arenas": args.arenas,
                         "fifo_plain": dict(fsum, trace_seconds=args.fifo_seconds), "fifo_results_agree": agree,
                         "saturation_sweep": sweep, "max_sustained_gbs": best["gbs"]},
+            "parity": {"ok": not bad, "checked": f"the first {len(jobs)} requests of the trace ({nb / 1e9:.1f} GB): "
+                                                 f"final state, match count and status vs the oracle",
+                       "mismatched_requests": bad[:8]},
+            "cpu_baseline": {"value": round(nb / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "sample": f"the first {len(jobs)} requests of the trace ({nb / 1e9:.1f} GB), independent "
+                                       f"oracle scans on {threads} host threads ({cpu_s:.1f} s)"},
             "e2e": {"value": main["gbs"], "unit": "GB/s", "h2d_bytes_per_step": int(len(req)) * 56,
                     "d2h_bytes_per_step": int(len(req)) * 64,
                     "note": "texts live in the device arena by design; each request's descriptor goes to the "
@@ -451,9 +538,37 @@ def run_serve(args, rank, world, local_rank):
             "gpu_launches": int(kernels),
             "clocks": clk,
         }
-        print(json.dumps(line), flush=True)
     for d in dfas:
         d.free()
+    del pools
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_batch(args, rank, world, local_rank):
+    import __graft_entry__ as ge
+
+    ge.build()
+    dev, dist = setup_rank(local_rank, world)
+    line = batch_measure(args, rank, world, dev, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_serve(args, rank, world, local_rank):
+    import __graft_entry__ as ge
+
+    ge.build()
+    dev, dist = setup_rank(local_rank, world)
+    line = serve_measure(args, rank, world, dev)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def run_ours(args, rank, world, local_rank):
@@ -463,13 +578,7 @@ def run_ours(args, rank, world, local_rank):
     import paper_1412_1741_gb300 as pm
 
     ge.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
+    dev, dist = setup_rank(local_rank, world)
     spec, text = make_workload(args.config, dev, seed_shift=rank)
     n = int(text.numel())
     dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
@@ -478,7 +587,7 @@ def run_ours(args, rank, world, local_rank):
     first = pm.parem_match(dfa, text)
     cap = max(1, first.match_count) if not args.count_only else 0
     pos = torch.empty(cap, dtype=torch.int64, device=dev) if cap else None
-    opts = pm.MatchOpts(segment_bytes=args.segment_bytes)  # the call a user makes
+    opts = pm.MatchOpts(segment_bytes=args.segment_bytes, enumerate_all=1 if args.enumerate else 0)
     for _ in range(args.warmup):
         pm.parem_match_ex(dfa, text, pos, opts)
     torch.cuda.synchronize()
@@ -503,7 +612,8 @@ def run_ours(args, rank, world, local_rank):
     kernels = args.steps * pm.parem_last_stats()["kernels"]
     # the kernel breakdown for the roofline: the same calls again with the library's own
     # CUDA events around pass 1 and the emit pass (outside the timed region above)
-    opts_timed = pm.MatchOpts(record_kernel_times=1, segment_bytes=args.segment_bytes)
+    opts_timed = pm.MatchOpts(record_kernel_times=1, segment_bytes=args.segment_bytes,
+                              enumerate_all=1 if args.enumerate else 0)
     scan_ms, emit_ms = [], []
     for _ in range(min(args.steps, 10)):
         pm.parem_match_ex(dfa, text, pos, opts_timed)
@@ -527,6 +637,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {
                 "workload": CONFIGS[args.config]["workload"], "text_bytes": n, "dfa_states": spec.n_states,
                 "matches": r.match_count, "positions": "all emitted" if cap else "count only",
+                "candidates": "all live states (enumeration)" if args.enumerate else "img(class of the previous byte)",
                 "l2": "inputs larger than L2 (text >> 126 MB), no flush needed" if n > (256 << 20) else
                       "input smaller than L2: resident between steps",
                 "segment_bytes": st["segment_bytes"], "chunks": st["chunks"], "blocks": st["blocks"],
@@ -542,10 +653,14 @@ def run_ours(args, rank, world, local_rank):
                 "emit_ms_avg": round(sum(emit_ms) / len(emit_ms), 4),
                 "traffic": profiled_traffic(args.config, n, st),
             },
+            "speculation": {"lookups_per_byte": round(st["spec_lookups"] / max(n, 1), 6),
+                            "spec_lookups": st["spec_lookups"], "main_run_bytes": n,
+                            "note": "table lookups of candidate runs before they merged (device counter), per "
+                                    "text byte; the resolved run adds one lookup per byte"},
             "gpu_launches": kernels,
             "clocks": clk,
         }
-    # end to end through the public API with host buffers (pinned), rank 0 style per rank
+    # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
         host_text = torch.empty(n, dtype=torch.uint8, pin_memory=True)
         host_text.copy_(text)
@@ -558,19 +673,42 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             re2e = pm.parem_match_host(dfa, host_text, host_pos)
             step_s.append(time.perf_counter() - t0)
-        step_s.sort()
+        link = host_link_gbs(host_text, text) if n >= (64 << 20) else None
         if rank == 0:
-            # median step: single steps of the host copy path now and then run at a fraction
-            # of the link rate on these hosts, in both the current and earlier builds
-            line["e2e"] = {"value": round(n / step_s[len(step_s) // 2] / 1e9, 2), "unit": "GB/s",
+            # the mean over the steps is the headline; the median and the measured host link
+            # (pinned host-to-device copy of the same buffer) are reported beside it
+            line["e2e"] = {"value": round(n * e2e_steps / sum(step_s) / 1e9, 2), "unit": "GB/s",
                            "h2d_bytes_per_step": n, "d2h_bytes_per_step": re2e.n_written * 8 + 24,
-                           "steps": e2e_steps, "statistic": "median step",
-                           "mean_value": round(n * e2e_steps / sum(step_s) / 1e9, 2)}
+                           "steps": e2e_steps, "statistic": "mean over steps",
+                           "median_value": round(n / sorted(step_s)[len(step_s) // 2] / 1e9, 2),
+                           "host_link_gbs": round(link, 2) if link else None}
         del host_text, host_pos
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(spec, text)
+        line["cpu_baseline"], line["parity"] = cpu_baseline_and_parity(spec, text, r, pos)
+    del text
+    dfa.free()
+    torch.cuda.empty_cache()
+    # the other two parts of the metric on the same GPU: batched vs plain, and serving
+    if world == 1 and args.config == "d2" and not args.no_extras and not args.size_mb:
+        b = batch_measure(args, rank, world, dev, None)
+        line["batched_vs_plain"] = dict(b["batched_vs_plain"], texts=b["config"]["texts"],
+                                        text_bytes=b["config"]["text_bytes"], dfas=b["config"]["dfas"],
+                                        p50_ms=b["p50_ms"], plan_seconds_with_autotune=b["config"]["plan_seconds_with_autotune"],
+                                        parity=b["parity"], cpu_baseline=b["cpu_baseline"], clocks=b["clocks"],
+                                        gpu_launches=b["gpu_launches"], roofline_frac=b["roofline"]["frac"])
+        line["gpu_launches"] += b["gpu_launches"]
+        v = serve_measure(args, rank, world, dev)
+        line["serving"] = dict(v["serving"], p50_ms=v["p50_ms"], p99_ms=v["p99_ms"], gbs=v["value"],
+                               parity=v["parity"], cpu_baseline=v["cpu_baseline"], clocks=v["clocks"],
+                               gpu_launches=v["gpu_launches"])
+        line["gpu_launches"] += v["gpu_launches"]
     if rank == 0:
         print(json.dumps(line), flush=True)
+        bad = [k for k in ("parity",) if k in line and not line[k]["ok"]]
+        bad += [k for k in ("batched_vs_plain", "serving") if k in line and not line[k]["parity"]["ok"]]
+        if bad:
+            print(f"PARITY FAILURE against the oracle in: {', '.join(bad)}", file=sys.stderr, flush=True)
+            sys.exit(3)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -688,6 +826,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
     ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
     ap.add_argument("--arenas", type=int, default=32, help="batches in flight in the serving configuration")
+    ap.add_argument("--serve-oracle-gb", type=float, default=20.0,
+                    help="bytes of the serving trace's first requests the oracle checks (GB)")
+    ap.add_argument("--enumerate", action="store_true",
+                    help="candidate set = every live state (the General Enumeration baseline)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without its batched and serving parts")
     ap.add_argument("--ncu-report", default="", help="summarise this --set full report into profiles/")
     ap.add_argument("--ncu-launches", default="", help="summarise this ncu --csv launch list into profiles/")
     ap.add_argument("--ncu-command", default="", help="the command that made the report (recorded)")

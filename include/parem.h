@@ -144,6 +144,12 @@ typedef struct {
   uint64_t cycles_spec, cycles_main, cycles_resolve;
   uint64_t cycles_bitmap, cycles_lane;  /* parts of cycles_spec: the bitmap phase of large
                                            candidate sets, the lane phase of the survivors */
+  /* Speculation work (the overhead of Algorithm 1's candidate runs over one run per byte):
+     table lookups by candidate runs before they merged, summed over rows -- counted as the
+     live candidates after each merge check times the steps to the next check, so an upper
+     bound within one check interval (4 or 16 steps) -- plus every candidate's run of a row
+     resolved through a slot map.  Divide by the text bytes for lookups per byte. */
+  uint64_t spec_lookups;
 } parem_stats;
 
 /*
@@ -172,7 +178,7 @@ int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
  * Regular expressions (host only, no GPU): the operators of the paper's Table III --
  * concatenation ab, Kleene star a*, union a|b, positive closure a+, range [0..9] (also
  * written [0-9]; [^..] negates a set), optionality a?, group ( ) -- compiled by the
- * McNaughton-Yamada-Thompson construction and the subset construction (Section IV) into a
+ * McNaughton-Yamada-Thompson construction and the subset construction (Section III) into a
  * DFA for parem_load_dfa, which is then minimized.  A byte stands for itself, '\' escapes the next one (\n \t \r
  * \0 \xHH), '.' is any byte, and an empty alternative matches the empty string.  Bytes
  * that every edge treats alike share one symbol, so the table has one column per class.
@@ -263,6 +269,9 @@ int parem_match_host(const parem_dfa* dfa, const uint8_t* text, uint64_t len, ui
  *   bytes per candidate per row.  With the default plan a 16 MiB area holds hundreds of MiB
  *   of text for the count, and about 100-150 MiB when positions are requested.
  *   Nothing is written to the outputs in that case.
+ *   Plans are those of parem_match for the same DFA: both entry points learn from every scan
+ *   (how long the DFA's candidates take to merge, how dense its matches are), so a DFA whose
+ *   earlier scans found dense matches gets the streaming emit pass here as well.
  *   Every GPU that loads the library holds the array until the process exits.  The first
  *   call on a device looks up the array's device address (cudaGetSymbolAddress, with that
  *   device current); make that first call before any stream capture begins.  All calls share

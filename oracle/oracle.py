@@ -6,8 +6,8 @@ product package: the two share no code, tables or helpers.
 
 Contents
 --------
-* ``scan``            -- the plain sequential DFA run (Section II-A; Section II-B "the basic
-                         idea of the sequential REM"), in C (``parem_oracle.c``) via ctypes.
+* ``scan``            -- the plain sequential DFA run (Section II-A; Section II-B: start in
+                         q0, one step per symbol), in C (``parem_oracle.c``) via ctypes.
 * ``scan_py``         -- the same definition as a pure-Python loop, for tiny cases.
 * ``trace``           -- the visited-state vector of one run (the vector Rr of Algorithm 1).
 * ``alg1_*``          -- Algorithm 1 restated step by step on the CPU for small inputs: the
@@ -94,8 +94,14 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def scan(table, byte_to_symbol, start, accept, text, want_positions=True, capacity=None) -> ScanResult:
-    """Plain sequential DFA run over ``text`` (C implementation)."""
+def scan(table, byte_to_symbol, start, accept, text, want_positions=True, capacity=None, times=None) -> ScanResult:
+    """Plain sequential DFA run over ``text`` (C implementation).
+
+    ``times``: optional list; the wall time (s) of each pass over the text is appended to it
+    (one pass without positions; with positions a counting pass, then the pass that writes
+    them), so that a caller can time one pass of the definition on its own."""
+    import time
+
     lib = _load()
     table, b2s, accept = _prep(table, byte_to_symbol, accept)
     text = np.ascontiguousarray(np.frombuffer(text, dtype=np.uint8) if isinstance(text, (bytes, bytearray)) else text,
@@ -105,18 +111,27 @@ def scan(table, byte_to_symbol, start, accept, text, want_positions=True, capaci
     cnt = ctypes.c_uint64()
     if want_positions:
         # First pass counts, second pass fills exactly; keeps memory bounded by the count.
+        t0 = time.perf_counter()
         rc = lib.oracle_dfa_scan(_ptr(table), table.shape[0], table.shape[1], _ptr(b2s), int(start),
                                  _ptr(accept), _ptr(text), n, None, 0, ctypes.byref(fs), ctypes.byref(cnt))
+        if times is not None:
+            times.append(time.perf_counter() - t0)
         if rc != 0:
             raise ValueError(f"oracle_dfa_scan: invalid argument ({rc})")
         cap = cnt.value if capacity is None else min(int(capacity), cnt.value)
         pos = np.zeros(max(cap, 1), dtype=np.uint64)
+        t0 = time.perf_counter()
         rc = lib.oracle_dfa_scan(_ptr(table), table.shape[0], table.shape[1], _ptr(b2s), int(start),
                                  _ptr(accept), _ptr(text), n, _ptr(pos), cap, ctypes.byref(fs), ctypes.byref(cnt))
+        if times is not None:
+            times.append(time.perf_counter() - t0)
         pos = pos[:cap]
     else:
+        t0 = time.perf_counter()
         rc = lib.oracle_dfa_scan(_ptr(table), table.shape[0], table.shape[1], _ptr(b2s), int(start),
                                  _ptr(accept), _ptr(text), n, None, 0, ctypes.byref(fs), ctypes.byref(cnt))
+        if times is not None:
+            times.append(time.perf_counter() - t0)
         pos = np.zeros(0, dtype=np.uint64)
     if rc != 0:
         raise ValueError(f"oracle_dfa_scan: invalid argument ({rc})")

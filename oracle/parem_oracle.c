@@ -6,8 +6,8 @@
  * header, table or helper with the CUDA path.
  *
  * What it computes is the plain definition of running a DFA (Q, Sigma, delta, q0, F) over a
- * text, one symbol at a time (Section II-A, the DFA quintuple; Section II-B, "the basic idea
- * of the sequential REM": start in q0 and take n steps).  There is no chunking and no
+ * text, one symbol at a time (Section II-A, the DFA quintuple; Section II-B, where the
+ * sequential run starts in q0 and takes one step per symbol).  There is no chunking and no
  * speculation here; the parallel method of Algorithm 1 must reproduce exactly this result.
  *
  * Readings of the paper that this file fixes:

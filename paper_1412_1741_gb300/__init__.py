@@ -99,7 +99,7 @@ class Stats(ctypes.Structure):
                 ("nonconv_rows", ctypes.c_uint32), ("conv_max", ctypes.c_uint32),
                 ("cycles_spec", ctypes.c_uint64), ("cycles_main", ctypes.c_uint64),
                 ("cycles_resolve", ctypes.c_uint64), ("cycles_bitmap", ctypes.c_uint64),
-                ("cycles_lane", ctypes.c_uint64)]
+                ("cycles_lane", ctypes.c_uint64), ("spec_lookups", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -647,6 +647,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   sc->stats.cycles_resolve = r.cyc_resolve;
   sc->stats.cycles_bitmap = r.cyc_bitmap;
   sc->stats.cycles_lane = r.cyc_lane;
+  sc->stats.spec_lookups = r.spec_lookups;
   if (pl.R) learn_convergence(dfa, pl.spec_cap, r.nonconv_rows, r.conv_max);
   if (len >= (1u << 20) && !r.error)
     const_cast<parem_dfa*>(dfa)->density_hint.store(

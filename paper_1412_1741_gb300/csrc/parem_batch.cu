@@ -708,6 +708,7 @@ extern "C" int parem_batch_stats(const parem_batch* batch, parem_stats* out) {
     out->cycles_resolve += r.cyc_resolve;
     out->cycles_bitmap += r.cyc_bitmap;
     out->cycles_lane += r.cyc_lane;
+    out->spec_lookups += r.spec_lookups;
   }
   out->kernels = batch_kernels(batch);
   return PAREM_OK;

@@ -142,6 +142,7 @@ struct DevResult {
   // maps), main run, resolution (waits, look-back, row records)
   unsigned long long cyc_spec, cyc_main, cyc_resolve;
   unsigned long long cyc_bitmap, cyc_lane;  // parts of cyc_spec: bitmap phase, lane phase
+  unsigned long long spec_lookups;          // lookups of candidate runs (see parem_stats)
 };
 static_assert(sizeof(DevResult) % 8 == 0, "the result word is copied in 8-byte words");
 

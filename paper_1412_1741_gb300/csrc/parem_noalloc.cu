@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -134,6 +135,9 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
   p.positions = emit ? positions : nullptr;
   p.capacity = emit ? capacity : 0;
+  // dense matches (learned from the DFA's earlier scans): the streaming emit pass, as in
+  // parem_match; it reads the same row records and needs no other scratch
+  p.stream_emit = (emit && pl.dense && pl.R) ? 1u : 0u;
 
   const bool global_table = P.layout == kClassGlobal || P.layout == kClassGlobalW;
   const size_t small_smem = kTableOff + (global_table ? 0 : P.table_bytes);
@@ -156,6 +160,12 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   if (cudaMemcpyAsync(&r, p.result, sizeof(DevResult), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PAREM_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PAREM_ERR_CUDA;
+  // what this scan taught about the DFA (how long its candidates took to merge, how dense its
+  // matches are) feeds the plans of later scans, whichever entry point makes them
+  if (pl.R) learn_convergence(dfa, pl.spec_cap, r.nonconv_rows, r.conv_max);
+  if (len >= (1u << 20) && !r.error)
+    const_cast<parem_dfa*>(dfa)->density_hint.store(
+        (uint32_t)std::min<uint64_t>(r.count / std::max<uint64_t>(1, len >> 20), 0xFFFFFFFEull));
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
   std::memset(out, 0, sizeof(*out));

@@ -2,7 +2,7 @@
 // concatenation, Kleene star, union, positive closure, range, optionality, group) compiled
 // to a DFA table for parem_load_dfa.
 //
-// The pipeline follows the paper's Section IV: the expression is parsed into a syntax tree
+// The pipeline follows the paper's Section III (Implementation): the expression is parsed into a syntax tree
 // by a recursive-descent parser of the operator grammar (precedence, lowest first: union,
 // concatenation, the postfix quantifiers * + ?); the tree becomes an NFA by the
 // McNaughton-Yamada-Thompson construction (one fragment per node, joined by empty

@@ -452,6 +452,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   };
 
   uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
+  // speculation work of this chunk (warp-uniform): live candidates after each merge check
+  // times the steps to the next check
+  unsigned long long spec_lk = 0;
   if constexpr (P == 1) {
     // 2. grouped speculation: G lanes per row, 32/G rows per pass
     const uint32_t G = p.group;
@@ -492,6 +495,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           done = true;
           outcome = 3;
         }
+#if PAREM_CONV_STATS
+        spec_lk += 16u * (uint32_t)__popc(__ballot_sync(kFull, !done && st != kEmpty));
+#endif
         const uint4 v = pos < staged ? staged16(kk, pos) : ra.get(grow, pos, (uint32_t)p.S);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -561,6 +567,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
       uint32_t st[P];
       uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
+      uint32_t live_n = m;  // live candidates after the last merge check (warp-uniform)
       uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
 #if PAREM_PHASE_STATS
       const uint32_t cb0 = (uint32_t)clock64();
@@ -589,6 +596,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
           const uint4 v = pos < staged ? staged16(k, pos) : ra.get(brow, pos, (uint32_t)p.S);
           if (pos >= staged) ra.shift(brow, pos, (uint32_t)p.S);
+#if PAREM_CONV_STATS
+          spec_lk += 16u * live_n;
+#endif
 #pragma unroll 1
           for (int q = 0; q < 16; ++q) {
             const uint32_t c = tab.col(byte_of(v, q));
@@ -623,6 +633,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           uint32_t local = 0;
           for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
           cnt = __reduce_add_sync(kFull, local);
+          live_n = cnt;
           if (cnt <= 32u * P) break;
         }
 #if PAREM_PHASE_STATS
@@ -676,6 +687,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         }
         const uint4 v = pos < staged ? staged16(k, pos) : wa.get(wrow, pos, (uint32_t)p.S);
         if (pos >= staged) wa.shift(wrow, pos, (uint32_t)p.S);
+#if PAREM_CONV_STATS
+        spec_lk += 16u * live_n;
+#endif
         if (p.bitmap_words) {
           // 16 steps with no merging inside them, then one merge of equal states across all
           // lanes and registers through the state bitmap, which also packs the survivors
@@ -711,6 +725,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
             if (lane >= (uint32_t)d) incl += o;
           }
           const uint32_t cnt = __shfl_sync(kFull, incl, 31);
+          live_n = cnt;
           uint32_t idx = incl - local;
           uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
           for (uint32_t w = lane; w < W; w += 32) {
@@ -798,6 +813,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           total = __popc(bl[0]);
           lr = 1;
         }
+        live_n = total;
         if (total <= 1) {
           outcome = 1;
           if (total == 0) {
@@ -848,7 +864,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
 #pragma unroll
         for (uint32_t i = 0; i < kLaneCand; ++i)
           ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
-        uint32_t L = my_hand, pos = my_t;
+        uint32_t L = my_hand, pos = my_t, lk2 = 0;
         bool busy = my_hand != 0;
         const uint8_t* lrow = body + (active ? myrow : row0) * p.S;
         RowAhead<(P >= 4)> la;
@@ -861,6 +877,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
           const uint32_t lmax = __reduce_max_sync(kFull, busy ? L : 0u);
           if (lmax == 0) break;
+          lk2 += busy ? 16u * L : 0u;
           const uint4 v = !busy ? make_uint4(0, 0, 0, 0) : pos < staged ? staged16(lane, pos) : la.get(lrow, pos, (uint32_t)p.S);
           if (busy && pos >= staged) la.shift(lrow, pos, (uint32_t)p.S);
 #pragma unroll
@@ -908,6 +925,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
         }
         my_hand = 0;
+#if PAREM_CONV_STATS
+        spec_lk += __reduce_add_sync(kFull, lk2);
+#endif
       }
       __syncwarp();
     }
@@ -926,6 +946,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     if (lane == 0) {
       if (nc) atomicAdd(&p.result->nonconv_rows, (uint32_t)__popc(nc));
       if (tmax) atomicMax(&p.result->conv_max, tmax);
+      if (spec_lk) atomicAdd(&p.result->spec_lookups, spec_lk);
     }
   }
 #endif
@@ -952,6 +973,10 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
     if (lane == 0) atomicAdd(&p.result->progress, 1u);
+#if PAREM_CONV_STATS
+    if (lane == 0)
+      atomicAdd(&p.result->spec_lookups, (unsigned long long)m * (p.S + (r == p.R - 1 ? p.tail : 0)));
+#endif
   }
 
 #if PAREM_PHASE_STATS

@@ -439,3 +439,34 @@ def test_regex_dfa_scan(torch, pattern, anchored):
     text = rng.choice(np.frombuffer(b"abcdxy0123.", np.uint8), size=(3 << 20) + 77)
     check(torch, spec, text, offset=3)
     check(torch, spec, text[:50_001], opts=pm.MatchOpts(segment_bytes=256))
+
+
+def test_text_longer_than_4gib_against_the_oracle(torch):
+    # The sparse-DFA workload at 4 GiB + 4,097 bytes viewed at an odd offset: row index x row
+    # length, the position bases and the chunk count pass 2^32 here.  Final state, count and
+    # every position are compared with the oracle's run over the same bytes, through the
+    # device entry point and through the host-buffer entry point (pieces, carry-in starts).
+    n = (4 << 30) + 4097
+    dev = torch.device("cuda")
+    src = wl.zipf_words_text_device(n, dev, seed=2, keywords=AC.meta["keywords"])
+    buf = torch.empty(n + 64, dtype=torch.uint8, device=dev)
+    view = buf[3:3 + n]
+    view.copy_(src)
+    del src
+    host = view.cpu().numpy()
+    want = oracle.scan(AC.table, AC.byte_to_symbol, AC.start, AC.accept, host)
+    assert want.match_count > 40_000 and int(want.positions[-1]) > (1 << 32)
+    dfa = load(AC)
+    pos = torch.full((want.match_count,), -1, dtype=torch.int64, device=dev)
+    got = pm.parem_match(dfa, view, pos)
+    assert (got.final_state, got.accepted, got.match_count, got.n_written) == \
+        (want.final_state, want.accepted, want.match_count, want.match_count)
+    assert np.array_equal(pos.cpu().numpy().view(np.uint64), want.positions)
+    st = pm.parem_last_stats()
+    assert st["rows"] * st["segment_bytes"] > (1 << 32)
+    del pos, buf, view
+    torch.cuda.empty_cache()
+    hpos = np.zeros(want.match_count, np.uint64)
+    got = pm.parem_match_host(dfa, host, hpos)
+    assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, want.match_count)
+    assert np.array_equal(hpos, want.positions)

@@ -184,3 +184,37 @@ def test_invalid_requests_are_rejected(torch, setup):
         srv.submit(null_text)
     assert srv.stats()["submitted"] == 0
     srv.free()
+
+
+def test_batches_overlap_on_the_device_and_each_result_equals_the_oracle(torch, setup):
+    # Continuous batching: a long request on the slowest random DFA occupies one arena; the
+    # short requests that arrive while it runs are admitted into later batches on other arenas
+    # and launched before the long one is done (their work overlaps on the device).  Every
+    # result, in the mix, equals the oracle's run of that request alone.
+    specs, dfas, pools = setup
+    slow = max((i for i, s in enumerate(specs) if s.meta["family"] == "random"), key=lambda i: specs[i].n_states)
+    big = wl.uniform_text_device(1 << 30, specs[slow].meta["alphabet"], torch.device("cuda"), seed=21)
+    n_small = 48
+    arrival = np.concatenate([[0], 2_000_000 + 250_000 * np.arange(n_small)]).astype(np.int64)
+    rng = np.random.default_rng(9)
+    dfa = np.concatenate([[slow], rng.integers(0, len(specs), size=n_small)]).astype(np.uint32)
+    length = np.concatenate([[big.numel()], rng.integers(1 << 10, 1 << 20, size=n_small)]).astype(np.int64)
+    addr = wl.serve_slices(specs, pools, dfa, length, seed=9)
+    addr[0] = big.data_ptr()
+    req = pm.make_requests(dfa, addr, length, arrival_ns=arrival)
+    srv = pm.parem_server_create(dfas)
+    resp = srv.replay(req)
+    st = srv.stats()
+    srv.free()
+    assert st["batches"] >= 2
+    launch0, done0 = int(resp["launch_ns"][0]), int(resp["done_ns"][0])
+    later = resp["launch_ns"][1:]
+    overlapped = np.nonzero((later > launch0) & (later < done0))[0] + 1
+    assert overlapped.size > 0, "no batch was launched while the long request's batch was running"
+    assert (resp["status"] == 0).all()
+    for i in range(len(req)):
+        spec = specs[int(dfa[i])]
+        text = big.cpu().numpy() if i == 0 else _view(pools, specs, req[i], torch).cpu().numpy()
+        o = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text, want_positions=False)
+        assert (int(resp["final_state"][i]), bool(resp["accepted"][i]), int(resp["match_count"][i])) == \
+            (o.final_state, o.accepted, o.match_count), i

@@ -1,5 +1,5 @@
 """Regular-expression front-end (host only, no GPU): the operators of Table III compiled by the
-Thompson and subset constructions (Section IV) into a DFA, checked by running that DFA with
+Thompson and subset constructions (Section III) into a DFA, checked by running that DFA with
 the oracle against a brute force with Python's `re` module (every position j such that some suffix of
 the text up to j, possibly empty, matches, or for anchored compilation the prefix up to j), and
 against the paper's own automaton of Table I for the literal "parallel"."""
