@@ -449,6 +449,10 @@ def test_text_longer_than_4gib_against_the_oracle(torch):
     n = (4 << 30) + 4097
     dev = torch.device("cuda")
     src = wl.zipf_words_text_device(n, dev, seed=2, keywords=AC.meta["keywords"])
+    # keywords planted past 2^32 (the last 4,097 bytes hold none at the generator's rate)
+    for k, at in enumerate((100, 1500, 3900)):
+        kw = AC.meta["keywords"][k]
+        src[(1 << 32) + at:(1 << 32) + at + len(kw)] = torch.frombuffer(bytearray(kw), dtype=torch.uint8).to(dev)
     buf = torch.empty(n + 64, dtype=torch.uint8, device=dev)
     view = buf[3:3 + n]
     view.copy_(src)

@@ -199,8 +199,8 @@ def test_batches_overlap_on_the_device_and_each_result_equals_the_oracle(torch, 
     rng = np.random.default_rng(9)
     dfa = np.concatenate([[slow], rng.integers(0, len(specs), size=n_small)]).astype(np.uint32)
     length = np.concatenate([[big.numel()], rng.integers(1 << 10, 1 << 20, size=n_small)]).astype(np.int64)
-    addr = wl.serve_slices(specs, pools, dfa, length, seed=9)
-    addr[0] = big.data_ptr()
+    addr = np.concatenate([[big.data_ptr()], wl.serve_slices(specs, pools, dfa[1:], length[1:], seed=9)])
+    addr = addr.astype(np.uint64)
     req = pm.make_requests(dfa, addr, length, arrival_ns=arrival)
     srv = pm.parem_server_create(dfas)
     resp = srv.replay(req)
