@@ -94,6 +94,9 @@ typedef struct {
                                random input (median of seeded trials; 0 when no set has two
                                states; 0xFFFFFFFF when a trial did not synchronise) */
   double mean_candidates;   /* mean candidate set size over the 256 byte values */
+  uint32_t pair_hot_states; /* > 0 once the two-byte stride variant (layout 8) has been learned
+                               from a text: its hot states; scans use it from then on */
+  uint32_t reserved;
 } parem_dfa_info;
 
 /* Options of parem_match_ex; zero-initialise, then set what you need. */
@@ -118,7 +121,17 @@ typedef struct {
   uint32_t record_kernel_times; /* 1: record CUDA events around each kernel of the call on the
                                    call's stream; read them with parem_last_stats */
   uint32_t use_start_state; /* 1: start from start_state instead of q0 */
+  uint32_t pair_mode;       /* the two-byte stride variant of a DFA with computed columns (layout
+                               7): PAREM_PAIR_AUTO (0) learns its hot states from the first scan
+                               of at least 64 MiB and uses it from the next scan on;
+                               PAREM_PAIR_LEARN (1) learns from this call's text (at least 4 KiB)
+                               if not learned yet; PAREM_PAIR_OFF (2) neither learns nor uses it
+                               in this call.  Results are the same in every mode. */
 } parem_match_opts;
+
+#define PAREM_PAIR_AUTO 0u
+#define PAREM_PAIR_LEARN 1u
+#define PAREM_PAIR_OFF 2u
 
 /* What the last scan on a (device, stream) did: its plan and, when record_kernel_times was
  * set, the device time of each kernel. */
@@ -150,6 +163,8 @@ typedef struct {
      bound within one check interval (4 or 16 steps) -- plus every candidate's run of a row
      resolved through a slot map.  Divide by the text bytes for lookups per byte. */
   uint64_t spec_lookups;
+  uint32_t layout;          /* table layout of the scan (8: the two-byte stride variant) */
+  uint32_t pair_hot_states; /* hot states of the two-byte stride table (layout 8), else 0 */
 } parem_stats;
 
 /*

@@ -34,6 +34,7 @@ __all__ = [
 
 PAREM_NONE = 0xFFFFFFFF
 PAREM_NONE16 = 0xFFFF
+PAREM_PAIR_AUTO, PAREM_PAIR_LEARN, PAREM_PAIR_OFF = 0, 1, 2
 PAREM_OK = 0
 PAREM_ERR_CAPACITY = -3
 PAREM_ERR_TOO_LARGE = -8
@@ -72,7 +73,8 @@ class _Info(ctypes.Structure):
                 ("has_dead", ctypes.c_uint32), ("entry_bytes", ctypes.c_uint32),
                 ("layout", ctypes.c_uint32), ("table_bytes", ctypes.c_uint32),
                 ("max_candidates", ctypes.c_uint32), ("sync_estimate", ctypes.c_uint32),
-                ("mean_candidates", ctypes.c_double)]
+                ("mean_candidates", ctypes.c_double), ("pair_hot_states", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class MatchOpts(ctypes.Structure):
@@ -80,14 +82,16 @@ class MatchOpts(ctypes.Structure):
                 ("segment_bytes", ctypes.c_uint64), ("warps_per_block", ctypes.c_uint32),
                 ("spec_cap_bytes", ctypes.c_uint32), ("wait_budget_cycles", ctypes.c_uint64),
                 ("debug_skip_publish_chunk", ctypes.c_int64), ("record_kernel_times", ctypes.c_uint32),
-                ("use_start_state", ctypes.c_uint32)]
+                ("use_start_state", ctypes.c_uint32), ("pair_mode", ctypes.c_uint32)]
 
     def __init__(self, start_state=PAREM_NONE, enumerate_all=0, segment_bytes=0, warps_per_block=0,
-                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=0, record_kernel_times=0):
+                 spec_cap_bytes=0, wait_budget_cycles=0, debug_skip_publish_chunk=0, record_kernel_times=0,
+                 pair_mode=0):
         # start_state PAREM_NONE: start at the DFA's q0
         use = 0 if start_state == PAREM_NONE else 1
         super().__init__(0 if not use else start_state, enumerate_all, segment_bytes, warps_per_block,
-                         spec_cap_bytes, wait_budget_cycles, debug_skip_publish_chunk, record_kernel_times, use)
+                         spec_cap_bytes, wait_budget_cycles, debug_skip_publish_chunk, record_kernel_times, use,
+                         pair_mode)
 
 
 class Stats(ctypes.Structure):
@@ -99,7 +103,8 @@ class Stats(ctypes.Structure):
                 ("nonconv_rows", ctypes.c_uint32), ("conv_max", ctypes.c_uint32),
                 ("cycles_spec", ctypes.c_uint64), ("cycles_main", ctypes.c_uint64),
                 ("cycles_resolve", ctypes.c_uint64), ("cycles_bitmap", ctypes.c_uint64),
-                ("cycles_lane", ctypes.c_uint64), ("spec_lookups", ctypes.c_uint64)]
+                ("cycles_lane", ctypes.c_uint64), ("spec_lookups", ctypes.c_uint64),
+                ("layout", ctypes.c_uint32), ("pair_hot_states", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -127,6 +132,7 @@ class DfaInfo:
     max_candidates: int
     mean_candidates: float
     sync_estimate: int = 0
+    pair_hot_states: int = 0
 
 
 def library_path() -> str:
@@ -219,7 +225,8 @@ class Dfa:
 
 def _info(i: _Info) -> DfaInfo:
     return DfaInfo(i.n_states, i.n_symbols, i.compact_states, i.n_classes, bool(i.has_dead), i.entry_bytes,
-                   i.layout, i.table_bytes, i.max_candidates, i.mean_candidates, i.sync_estimate)
+                   i.layout, i.table_bytes, i.max_candidates, i.mean_candidates, i.sync_estimate,
+                   i.pair_hot_states)
 
 
 def parem_prepare_info(table, byte_to_symbol, start, accept) -> DfaInfo:

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libparem.so")
 SOURCES = ["parem_api.cu", "parem_prep.cpp", "parem_k_byte.cu", "parem_k_class.cu", "parem_k_global.cu",
            "parem_noalloc.cu", "parem_k_batch.cu", "parem_batch.cu", "parem_server.cpp", "parem_k_win.cu",
-           "parem_regex.cpp"]
+           "parem_regex.cpp", "parem_k_pair.cu", "parem_pair.cpp"]
 HEADERS = ["parem_internal.h", "parem_launch.h", "parem_scan.cuh", "parem_batch_impl.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

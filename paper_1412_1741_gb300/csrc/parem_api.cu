@@ -152,6 +152,81 @@ void fill_info(const Prepared& P, parem_dfa_info* info) {
 
 }  // namespace
 
+namespace parem {
+
+int upload_prepared(const Prepared& P, DeviceDfa* out, void** dmem) {
+  // one allocation: table | colmap | byte_class | img_off | img | rank
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = round_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_table = take(P.table.size());
+  const bool wide = P.layout == kClassSmemW || P.layout == kClassGlobalW;
+  std::vector<uint8_t> cm(512, 0);
+  for (int b = 0; b < 256; ++b) {
+    if (wide) {
+      std::memcpy(&cm[2 * b], &P.colmap[b], 2);
+    } else {
+      cm[b] = (uint8_t)P.colmap[b];
+    }
+  }
+  const size_t o_colmap = take(512);
+  const size_t o_cls = take(256 * 2);
+  const size_t o_imgoff = take(P.img_off.size() * 4);
+  const size_t o_img = take(P.img.size() * 2);
+  const size_t o_rank = take(P.rank.size() * 2);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) return PAREM_ERR_OOM;
+  uint8_t* base = static_cast<uint8_t*>(mem);
+  cudaError_t e = cudaSuccess;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_table, P.table.data(), P.table.size(), cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_colmap, cm.data(), 512, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_cls, P.byte_class.data(), 256 * 2, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_imgoff, P.img_off.data(), P.img_off.size() * 4, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_img, P.img.data(), P.img.size() * 2, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_rank, P.rank.data(), P.rank.size() * 2, cudaMemcpyHostToDevice) : e;
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return PAREM_ERR_CUDA;
+  }
+  DeviceDfa D{};
+  D.table = base + o_table;
+  D.colmap = base + o_colmap;
+  D.byte_class = reinterpret_cast<const uint16_t*>(base + o_cls);
+  D.img_off = reinterpret_cast<const uint32_t*>(base + o_imgoff);
+  D.img = reinterpret_cast<const uint16_t*>(base + o_img);
+  D.rank = reinterpret_cast<const uint16_t*>(base + o_rank);
+  D.n = P.n;
+  D.n_classes = P.n_classes;
+  D.first_accept = P.first_accept;
+  D.dead = P.dead;
+  D.start = P.start;
+  D.layout = P.layout;
+  D.esize = P.esize;
+  D.rowbytes = P.rowbytes;
+  D.table_bytes = P.table_bytes;
+  D.max_cand = P.max_cand;
+  D.stride_k = P.stride_k;
+  D.stride_off = P.stride_off;
+  {
+    const uint32_t K = P.stride_k;
+    D.stride_k4 = K * K * K * K;
+    D.stride_wts = K <= 6 ? (K * K * K | (K * K) << 8 | K << 16 | 1u << 24) : 0u;
+    D.stride_krep = K * 0x01010101u;
+    D.stride_kmrep = K ? (K - 1) * 0x01010101u : 0u;
+  }
+  D.win = P.win;
+  D.pair_hot = P.pair_hot;
+  D.pair_off = P.pair_off;
+  *out = D;
+  *dmem = mem;
+  return PAREM_OK;
+}
+
+}  // namespace parem
+
 // =======================================================================================
 // ABI
 // =======================================================================================
@@ -200,72 +275,11 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
     delete d;
     return PAREM_ERR_CUDA;
   }
-  // one allocation: table | colmap | byte_class | img_off | img | rank
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    size_t o = off;
-    off = round_up(off + bytes, 256);
-    return o;
-  };
-  const size_t o_table = take(P.table.size());
-  const bool wide = P.layout == kClassSmemW || P.layout == kClassGlobalW;
-  std::vector<uint8_t> cm(512, 0);
-  for (int b = 0; b < 256; ++b) {
-    if (wide) {
-      std::memcpy(&cm[2 * b], &P.colmap[b], 2);
-    } else {
-      cm[b] = (uint8_t)P.colmap[b];
-    }
-  }
-  const size_t o_colmap = take(512);
-  const size_t o_cls = take(256 * 2);
-  const size_t o_imgoff = take(P.img_off.size() * 4);
-  const size_t o_img = take(P.img.size() * 2);
-  const size_t o_rank = take(P.rank.size() * 2);
-  if (cudaMalloc(&d->dmem, off) != cudaSuccess) {
+  rc = upload_prepared(P, &d->dev, &d->dmem);
+  if (rc != PAREM_OK) {
     delete d;
-    return PAREM_ERR_OOM;
+    return rc;
   }
-  uint8_t* base = static_cast<uint8_t*>(d->dmem);
-  cudaError_t e = cudaSuccess;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_table, P.table.data(), P.table.size(), cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_colmap, cm.data(), 512, cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_cls, P.byte_class.data(), 256 * 2, cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_imgoff, P.img_off.data(), P.img_off.size() * 4, cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_img, P.img.data(), P.img.size() * 2, cudaMemcpyHostToDevice) : e;
-  e = e == cudaSuccess ? cudaMemcpy(base + o_rank, P.rank.data(), P.rank.size() * 2, cudaMemcpyHostToDevice) : e;
-  if (e != cudaSuccess) {
-    cudaFree(d->dmem);
-    delete d;
-    return PAREM_ERR_CUDA;
-  }
-  DeviceDfa& D = d->dev;
-  D.table = base + o_table;
-  D.colmap = base + o_colmap;
-  D.byte_class = reinterpret_cast<const uint16_t*>(base + o_cls);
-  D.img_off = reinterpret_cast<const uint32_t*>(base + o_imgoff);
-  D.img = reinterpret_cast<const uint16_t*>(base + o_img);
-  D.rank = reinterpret_cast<const uint16_t*>(base + o_rank);
-  D.n = P.n;
-  D.n_classes = P.n_classes;
-  D.first_accept = P.first_accept;
-  D.dead = P.dead;
-  D.start = P.start;
-  D.layout = P.layout;
-  D.esize = P.esize;
-  D.rowbytes = P.rowbytes;
-  D.table_bytes = P.table_bytes;
-  D.max_cand = P.max_cand;
-  D.stride_k = P.stride_k;
-  D.stride_off = P.stride_off;
-  {
-    const uint32_t K = P.stride_k;
-    D.stride_k4 = K * K * K * K;
-    D.stride_wts = K <= 6 ? (K * K * K | (K * K) << 8 | K << 16 | 1u << 24) : 0u;
-    D.stride_krep = K * 0x01010101u;
-    D.stride_kmrep = K ? (K - 1) * 0x01010101u : 0u;
-  }
-  D.win = P.win;
   fill_info(P, &d->info);
   *out = d;
   return PAREM_OK;
@@ -274,6 +288,8 @@ extern "C" int parem_load_dfa(const uint32_t* table, uint32_t n_states, uint32_t
 extern "C" int parem_dfa_get_info(const parem_dfa* dfa, parem_dfa_info* info) {
   if (!dfa || !info) return PAREM_ERR_INVALID_ARG;
   *info = dfa->info;
+  info->pair_hot_states =
+      dfa->pair_state.load(std::memory_order_acquire) == kPairReady ? dfa->pair_host.pair_hot : 0u;
   return PAREM_OK;
 }
 
@@ -282,6 +298,7 @@ extern "C" void parem_free_dfa(parem_dfa* dfa) {
   cudaDeviceSynchronize();
   if (dfa->dmem) cudaFree(dfa->dmem);
   if (dfa->batch_mem) cudaFree(dfa->batch_mem);
+  if (dfa->pair_mem) cudaFree(dfa->pair_mem);
   delete dfa;
 }
 
@@ -391,9 +408,15 @@ void learn_convergence(const parem_dfa* dfa, uint32_t spec_cap, uint32_t nonconv
 
 int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const parem_match_opts* o,
               Plan* pl) {
-  const Prepared& P = dfa->host;
   const DevProps props = dev_props(dfa->device);
   std::memset(pl, 0, sizeof(*pl));
+  // the two-byte stride variant once it has been learned (and unless the call declines it)
+  const bool pair = !(o && o->pair_mode == PAREM_PAIR_OFF) &&
+                    dfa->pair_state.load(std::memory_order_acquire) == kPairReady;
+  pl->prep = pair ? &dfa->pair_host : &dfa->host;
+  pl->ddfa = pair ? &dfa->pair_dev : &dfa->dev;
+  const Prepared& P = *pl->prep;
+  pl->layout = P.layout;
   pl->enum_all = o && o->enumerate_all ? 1u : 0u;
   const uint32_t m_need = pl->enum_all ? (P.n - P.has_dead) : P.max_cand;
   pl->P = m_need <= 32 ? 1 : m_need <= 64 ? 2 : m_need <= 128 ? 4 : 8;
@@ -421,7 +444,8 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   pl->spec_bytes = kSpecBytes + (pl->bitmap_words ? (uint32_t)round_up(8ull * pl->bitmap_words, 16) + 512u : 0u);
   const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + pl->spec_bytes;
   int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
-  warps = std::min(warps, pl->P >= 4 ? 24 : 32);  // the launch bounds of the kernel variants
+  // the launch bounds of the kernel variants
+  warps = std::min(warps, P.layout == kClassPair ? (int)kPairMaxWarps : pl->P >= 4 ? 24 : 32);
   if (o && o->warps_per_block) warps = std::min<int>(warps, (int)o->warps_per_block);
   if (warps < 1) return PAREM_ERR_UNSUPPORTED;
   pl->warps = warps;
@@ -492,21 +516,22 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
 static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uint64_t* positions,
                     uint64_t capacity, const parem_match_opts* o, cudaStream_t stream, parem_result* out,
                     uint64_t pos_base = 0) {
-  const Prepared& P = dfa->host;
-  uint32_t init = P.start;
-  if (o && o->use_start_state) {
-    if (o->start_state >= P.n_in) return PAREM_ERR_INVALID_ARG;
-    init = P.compact_of[o->start_state];
-  }
+  if (o && o->use_start_state && o->start_state >= dfa->host.n_in) return PAREM_ERR_INVALID_ARG;
   std::memset(out, 0, sizeof(*out));
   if (len == 0) {
-    out->final_state = P.orig_of[init];
-    out->accepted = init >= P.first_accept;
+    const Prepared& P0 = dfa->host;
+    const uint32_t init0 = (o && o->use_start_state) ? P0.compact_of[o->start_state] : P0.start;
+    out->final_state = P0.orig_of[init0];
+    out->accepted = init0 >= P0.first_accept;
     return PAREM_OK;
   }
   Plan pl;
   int rc = plan_scan(dfa, text, len, o, &pl);
   if (rc != PAREM_OK) return rc;
+  // the prepared DFA of this scan (the two-byte stride variant when it is used): its state
+  // numbering applies to the start state and the result
+  const Prepared& P = *pl.prep;
+  const uint32_t init = (o && o->use_start_state) ? P.compact_of[o->start_state] : P.start;
   Scratch* sc = get_scratch(dfa->device, stream);
   if (!sc) return PAREM_ERR_OOM;
   if (!sc->host_res) {
@@ -558,7 +583,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
 
   ScanParams p;
   std::memset(&p, 0, sizeof(p));
-  p.dfa = dfa->dev;
+  p.dfa = *pl.ddfa;
   p.text = text;
   p.n = len;
   p.h = pl.h;
@@ -612,6 +637,8 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   sc->stats.candidate_regs = pl.P;
   sc->stats.spec_cap_bytes = pl.spec_cap;
   sc->stats.kernels = 1 + ((pl.R && emit) ? 1 : 0);
+  sc->stats.layout = P.layout;
+  sc->stats.pair_hot_states = P.layout == kClassPair ? P.pair_hot : 0u;
   if (timed) PAREM_CUDA_TRY(cudaEventRecord(sc->ev[0], stream));
   cudaError_t e;
   if (pl.R == 0) {
@@ -652,6 +679,14 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   if (len >= (1u << 20) && !r.error)
     const_cast<parem_dfa*>(dfa)->density_hint.store(
         (uint32_t)std::min<uint64_t>(r.count / std::max<uint64_t>(1, len >> 20), 0xFFFFFFFEull));
+  // a large text (or a call that asks) teaches a computed-column DFA its hot states once; the
+  // two-byte stride variant is used from the next scan on
+  if (!r.error && dfa->host.layout == kClassWin && !(o && o->pair_mode == PAREM_PAIR_OFF) &&
+      (len >= kPairLearnBytes || (o && o->pair_mode == PAREM_PAIR_LEARN && len >= 4096))) {
+    uint32_t expect = kPairNone;
+    parem_dfa* md = const_cast<parem_dfa*>(dfa);
+    if (md->pair_state.compare_exchange_strong(expect, kPairBusy)) learn_pairs(md, text, len, stream);
+  }
   if (r.error == kErrTimeout) return PAREM_ERR_TIMEOUT;
   if (r.error) return PAREM_ERR_INTERNAL;
   const uint32_t fs = r.final_state;

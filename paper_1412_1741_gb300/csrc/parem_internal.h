@@ -36,7 +36,20 @@ enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClass
                          kByteStride = 6,
                          // class table in shared memory whose columns are computed from the byte:
                          // bytes [lo, lo + w) -> columns 2.., byte xb -> column 1, others column 0
-                         kClassWin = 7 };
+                         kClassWin = 7,
+                         // kClassWin plus a two-byte stride table over the hot states for the main
+                         // run (texts of lowercase letters and spaces; see the pair table below)
+                         kClassPair = 8 };
+// Two-byte stride ("pair") table of kClassPair.  A byte b of {0x20, 0x61..0x7A} has the code
+// f = b & 0x1F (0 for the space, 1..26 for a..z); two bytes form the pair index 27 f0 + f1.
+// The hot states are the compact states 0 .. H-1 (non-accepting, the most visited ones); row
+// e < H holds, for every pair, the hot state reached after both bytes, or the escape value H
+// when an intermediate or final state is accepting or not hot.  Row H is all H, so an escaped
+// run stays escaped.  Entries are bytes; H <= 127.
+constexpr uint32_t kPairCodes = 27;
+constexpr uint32_t kPairRow = kPairCodes * kPairCodes;  // 729 entries per row
+constexpr uint32_t kPairMaxHot = 127;
+constexpr uint32_t kPairMaxWarps = 16;  // warps per block of its pass 1 (its tables leave no room for more)
 constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
 // Shared memory of every kernel starts with the column map (512 B reserved) followed by the
 // table at this fixed offset, so table reads use an immediate offset.
@@ -69,7 +82,10 @@ struct Prepared {
   uint32_t sync_len = 0;            // estimated synchronisation length (symbols), or kNoSync
   uint32_t stride_k = 0;            // kByteStride: symbols K of the stride table (byte b -> min(b, K-1))
   uint32_t stride_off = 0;          // kByteStride: offset of the stride table inside `table`
-  uint32_t win = 0;                 // kClassWin: lo | w << 8 | xb << 16
+  uint32_t win = 0;                 // kClassWin, kClassPair: lo | w << 8 | xb << 16
+  uint32_t pair_hot = 0;            // kClassPair: hot states H (escape value)
+  uint32_t pair_off = 0;            // kClassPair: offset of the pair table inside `table`
+  uint32_t main_bytes = 0;          // kClassPair: bytes of the class table before the pair table
   std::vector<uint32_t> orig_of;    // compact -> original (dead -> 0xFFFFFFFF)
   std::vector<uint32_t> compact_of; // original -> compact
   std::vector<uint16_t> byte_class; // 256
@@ -101,6 +117,7 @@ struct DeviceDfa {
   // K <= 6, and K and K - 1 in every byte
   uint32_t stride_k4, stride_wts, stride_krep, stride_kmrep;
   uint32_t win;                   // kClassWin (see Prepared)
+  uint32_t pair_hot, pair_off;    // kClassPair (see Prepared)
 };
 
 // Per-segment record for the emit pass: the matches of the row lie in the row-relative

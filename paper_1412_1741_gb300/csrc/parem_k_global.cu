@@ -38,6 +38,7 @@ cudaError_t launch_scan_dispatch(uint32_t layout, uint32_t esize, uint32_t P, co
   switch (layout) {
     case kByteSmem: return scan_byte(esize, P, tm, p, grid, block, smem, s);
     case kClassWin: return scan_win(esize, P, tm, p, grid, block, smem, s);
+    case kClassPair: return scan_pair(esize, P, tm, p, grid, block, smem, s);
     case kByteStride:
       // at most 32 compact states, so at most 32 candidates (P == 1); anything else would be
       // a planning error
@@ -54,7 +55,8 @@ cudaError_t launch_emit_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return emit_byte(esize, p, tm, grid, block, smem, s);
     case kByteStride: return emit_byte_stride(p, tm, grid, block, smem, s);
-    case kClassWin: return emit_win(esize, p, tm, grid, block, smem, s);
+    case kClassWin:
+    case kClassPair: return emit_win(esize, p, tm, grid, block, smem, s);
     case kClassSmem: return emit_class(esize, p, tm, grid, block, smem, s);
     case kClassSmemW: return emit_class_wide(p, tm, grid, block, smem, s);
     case kClassGlobal: return emit_global(0, p, tm, grid, block, smem, s);
@@ -67,7 +69,8 @@ cudaError_t launch_tiny_dispatch(uint32_t layout, uint32_t esize, const ScanPara
   switch (layout) {
     case kByteSmem: return tiny_byte(esize, p, smem, s);
     case kByteStride: return tiny_byte_stride(p, smem, s);
-    case kClassWin: return tiny_win(esize, p, smem, s);
+    case kClassWin:
+    case kClassPair: return tiny_win(esize, p, smem, s);
     case kClassSmem: return tiny_class(esize, p, smem, s);
     case kClassSmemW: return tiny_class_wide(p, smem, s);
     case kClassGlobal: return tiny_global(0, p, smem, s);

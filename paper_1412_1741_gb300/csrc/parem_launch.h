@@ -27,6 +27,15 @@ struct parem_dfa {
   // matches per MiB of text in the last scan of at least 1 MiB (kEmpty: none yet); scans
   // of DFAs that matched rarely count matches only in the 16-byte vectors that have one
   std::atomic<uint32_t> density_hint{0xFFFFFFFFu};
+  // The two-byte stride variant (kClassPair) of a kClassWin DFA, learned once from a sample
+  // of a large text: a copy of the prepared DFA renumbered with the most visited states
+  // first, its pair table appended, and its device copy.  pair_state: kPairNone (not tried),
+  // kPairBusy (being built by one call), kPairReady (pair_host / pair_dev usable, never
+  // changed again), kPairOff (not worth it for the texts seen).
+  std::atomic<uint32_t> pair_state{0};
+  parem::Prepared pair_host;
+  parem::DeviceDfa pair_dev{};
+  void* pair_mem = nullptr;
 };
 
 namespace parem {
@@ -51,11 +60,24 @@ uint64_t max_row_bytes(const parem_dfa* dfa, uint32_t m);
 bool serial_rows(const parem_dfa* dfa, uint32_t m);
 // Record what a scan with the given speculation cap observed about convergence.
 void learn_convergence(const parem_dfa* dfa, uint32_t spec_cap, uint32_t nonconv_rows, uint32_t conv_max);
+
+constexpr uint32_t kPairNone = 0, kPairBusy = 1, kPairReady = 2, kPairOff = 3;
+// Texts at least this long teach a kClassWin DFA its hot states (parem_pair.cpp).
+constexpr uint64_t kPairLearnBytes = 64ull << 20;
+// Sample the device text, choose the hot states, build and upload the kClassPair variant when
+// it pays (parem_pair.cpp); sets pair_state to kPairReady or kPairOff.  Host call, blocking.
+int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t stream);
+// The device copy of a prepared DFA: one allocation (table, column map, byte classes,
+// candidate lists, ranks) and the DeviceDfa that points into it (parem_api.cu).
+int upload_prepared(const Prepared& P, DeviceDfa* D, void** dmem);
 }  // namespace parem
 
 namespace parem {
 
 struct Plan {
+  const Prepared* prep;  // the prepared DFA the scan runs (the pair variant when it is used)
+  const DeviceDfa* ddfa; // and its device copy
+  uint32_t layout;       // its table layout
   uint32_t P;            // candidate registers per lane in the warp-wide phase (1, 2, 4, 8)
   uint32_t enum_all;
   uint32_t cand_stride;
@@ -111,6 +133,8 @@ cudaError_t scan_win(uint32_t esize, uint32_t P, const CUtensorMap& tm, const Sc
 cudaError_t emit_win(uint32_t esize, const ScanParams& p, const CUtensorMap* tm,
                      int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t tiny_win(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
+cudaError_t scan_pair(uint32_t esize, uint32_t P, const CUtensorMap& tm, const ScanParams& p, int grid, int block,
+                      size_t smem, cudaStream_t s);
 cudaError_t tiny_class(uint32_t esize, const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_class_wide(const ScanParams& p, size_t smem, cudaStream_t s);
 cudaError_t tiny_global(uint32_t wide, const ScanParams& p, size_t smem, cudaStream_t s);

@@ -80,17 +80,19 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   void* area = nullptr;
   int rc = scratch_address(dev, &area);
   if (rc != PAREM_OK) return rc;
-  const Prepared& P = dfa->host;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (len == 0) {
+    const Prepared& P0 = dfa->host;
     std::memset(out, 0, sizeof(*out));
-    out->final_state = P.orig_of[P.start];
-    out->accepted = P.start >= P.first_accept;
+    out->final_state = P0.orig_of[P0.start];
+    out->accepted = P0.start >= P0.first_accept;
     return PAREM_OK;
   }
   Plan pl;
   rc = plan_scan(dfa, text, len, nullptr, &pl);
   if (rc != PAREM_OK) return rc;
+  // the prepared DFA of this scan (its two-byte stride variant once parem_match has learned it)
+  const Prepared& P = *pl.prep;
   // the layout of parem_match's scratch, inside the fixed area
   const bool emit = positions != nullptr && capacity > 0;
   const uint64_t o_status = 512;
@@ -106,7 +108,7 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
 
   ScanParams p;
   std::memset(&p, 0, sizeof(p));
-  p.dfa = dfa->dev;
+  p.dfa = *pl.ddfa;
   p.text = text;
   p.n = len;
   p.h = pl.h;

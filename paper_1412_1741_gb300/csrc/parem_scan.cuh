@@ -151,7 +151,7 @@ struct Tab {
   static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW;
   static constexpr bool kDyn = LAYOUT == kBatchDyn;
   static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW || LAYOUT == kBatchDyn;
-  static constexpr bool kWin = LAYOUT == kClassWin;
+  static constexpr bool kWin = LAYOUT == kClassWin || LAYOUT == kClassPair;
   const uint8_t* sm;       // dynamic shared memory base
   const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
@@ -1018,6 +1018,37 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       for (uint32_t i = 0; i < kBox / 16; ++i) {
         const uint32_t col = col0 + i * 16u;
         if (col >= my_t) {
+          bool exact = true;  // the vector is run byte by byte below
+          if constexpr (LAYOUT == kClassPair) {
+            // Two bytes per lookup while the run stays in the hot states and every byte is a
+            // space or a lowercase letter.  Each word's codes f = b & 0x1F index the pair table
+            // by one byte dot product (27 f0 + f1, 27 f2 + f3) on top of the row base.  The
+            // fold is exact only for {0x20, 0x61..0x7A}: per byte, bit 7 must be clear, bit 5
+            // set, bit 6 equal to (f != 0) and f < 27; any other byte, and any escape (a
+            // cold or accepting state within the vector), sends the vector to the byte loop
+            // from its start state.  A vector taken here has no match (hot states are not
+            // accepting and the table escapes on an accepting step).
+            const uint32_t H = D.pair_hot, t2 = D.pair_off;
+            const uint32_t ws[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+            uint32_t e = min(s, H);
+            uint32_t acc_a = 0, acc_b = 0, acc_c = 0xFFFFFFFFu;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const uint32_t w = ws[g];
+              const uint32_t f = w & 0x1F1F1F1Fu;
+              acc_a |= (f + 0x3F3F3F3Fu) ^ w;  // bit 7: b >= 0x80; bit 6: bit 6 of b != (f != 0)
+              acc_b |= f + 0x65656565u;        // bit 7: f >= 27
+              acc_c &= w;                      // bit 5 must stay set
+              e = sm[kTableOff + __dp4a(f, 0x0000011Bu, e * kPairRow + t2)];
+              e = sm[kTableOff + __dp4a(f, 0x011B0000u, e * kPairRow + t2)];
+            }
+            const uint32_t bad = (acc_a & 0xC0C0C0C0u) | (acc_b & 0x80808080u) | (~acc_c & 0x20202020u);
+            if (bad == 0u && e < H) {
+              s = e;
+              exact = false;
+            }
+          }
+          if (exact) {
           const uint32_t mu0 = mu, s0 = s;
           if constexpr (LAYOUT == kByteStride) {
             // four bytes per lookup: the stride table holds the state after them and how
@@ -1093,6 +1124,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
                 }
               }
             }
+          }
           }
         }
       }
@@ -1440,8 +1472,15 @@ __device__ __forceinline__ void clear_prev_header(const ScanParams& p) {
     p.clear[i] = make_uint4(0, 0, 0, 0);
 }
 
+// Threads per block the pass-1 kernel is compiled for: the pair variant's tables leave room
+// for at most kPairMaxWarps warps, so it gets the registers of 512 threads.
+template <int LAYOUT, int P>
+constexpr int spec_scan_threads() {
+  return LAYOUT == kClassPair ? (int)(kPairMaxWarps * 32) : (P >= 4 ? 768 : 1024);
+}
+
 template <int LAYOUT, int ESIZE, int P>
-__global__ void __launch_bounds__(P >= 4 ? 768 : 1024, 1)
+__global__ void __launch_bounds__(spec_scan_threads<LAYOUT, P>(), 1)
     k_spec_scan(const __grid_constant__ CUtensorMap tmap, const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint8_t* const sm = smem_raw;

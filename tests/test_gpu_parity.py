@@ -474,3 +474,89 @@ def test_text_longer_than_4gib_against_the_oracle(torch):
     got = pm.parem_match_host(dfa, host, hpos)
     assert (got.final_state, got.match_count, got.n_written) == (want.final_state, want.match_count, want.match_count)
     assert np.array_equal(hpos, want.positions)
+
+
+def _pair_spec(n_keywords=64, seed=1):
+    if n_keywords == 64 and seed == 1:
+        return AC
+    kws = wl.random_keywords(n_keywords, 3, 10, seed=seed)
+    sym = wl.letters_byte_map()
+    t, acc = wl.aho_corasick_dfa([[int(sym[b]) for b in kw] for kw in kws], 27)
+    return wl.DfaSpec(t, 0, acc, sym, f"ac{n_keywords}-{seed}", {"keywords": kws})
+
+
+@pytest.mark.parametrize("n_keywords,seed", [(64, 1), (12, 5), (40, 9)])
+def test_two_byte_stride_variant(torch, n_keywords, seed):
+    # The two-byte stride variant (layout 8) of a computed-column keyword DFA, learned from the
+    # first text: scans that use it give the oracle's result on texts of letters and spaces,
+    # texts with every other kind of byte sprinkled in (each sends its vector to the byte loop),
+    # texts dense with keywords (escapes through accepting states), carry-in starts, capacity
+    # limits, count-only calls and forced row lengths.
+    spec = _pair_spec(n_keywords, seed)
+    kws = spec.meta["keywords"]
+    dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    assert pm.parem_dfa_get_info(dfa).layout == 7
+    learn_text = wl.zipf_words_text(6 << 20, seed_words=3, seed_plants=4, plant_rate=1e-4, keywords=kws)
+    _, lview = device_text(torch, learn_text, 0)
+    first = pm.parem_match_ex(dfa, lview, None, pm.MatchOpts(pair_mode=pm.PAREM_PAIR_LEARN), length=learn_text.size)
+    assert pm.parem_last_stats()["layout"] == 7  # the scan that learns still runs layout 7
+    want0 = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, learn_text, want_positions=False)
+    assert (first.final_state, first.match_count) == (want0.final_state, want0.match_count)
+    hot = pm.parem_dfa_get_info(dfa).pair_hot_states
+    assert 2 <= hot <= 127
+    rng = np.random.default_rng(seed)
+    plain = wl.zipf_words_text((3 << 20) + 11, seed_words=7, seed_plants=8, plant_rate=3e-4, keywords=kws)
+    noisy = plain.copy()
+    odd = np.array([0x00, 0x1F, 0x21, 0x3A, 0x3F, 0x40, 0x41, 0x5A, 0x5F, 0x60, 0x7B, 0x7E, 0x7F, 0x80, 0xC1, 0xE0,
+                    0xFA, 0xFF], np.uint8)
+    where = rng.random(noisy.size) < 2e-4
+    noisy[where] = rng.choice(odd, size=int(where.sum()))
+    dense = plain.copy()
+    p = 5000
+    while p < 400_000:  # a keyword every few bytes
+        kw = kws[int(rng.integers(len(kws)))]
+        dense[p:p + len(kw)] = np.frombuffer(kw, np.uint8)
+        p += len(kw) + int(rng.integers(0, 4))
+    for text, offset, opts in ((plain, 3, None), (noisy, 0, None), (dense, 5, None),
+                               (plain, 7, pm.MatchOpts(segment_bytes=1024)), (noisy, 1, pm.MatchOpts(segment_bytes=128))):
+        want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
+        _, view = device_text(torch, text, offset)
+        for cap in (max(1, want.match_count), max(1, want.match_count // 3)):
+            pos = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+            got = pm.parem_match_ex(dfa, view, pos, opts, length=text.size)
+            assert pm.parem_last_stats()["layout"] == 8
+            assert (got.final_state, got.accepted, got.match_count) == (want.final_state, want.accepted, want.match_count)
+            k = min(cap, want.match_count)
+            assert got.n_written == k
+            assert np.array_equal(pos[:k].cpu().numpy().view(np.uint64), want.positions[:k])
+        cnt = pm.parem_match_ex(dfa, view, None, opts, length=text.size)
+        assert (cnt.final_state, cnt.match_count) == (want.final_state, want.match_count)
+        # the plain variant, declined for one call, agrees
+        off = pm.parem_match_ex(dfa, view, None, pm.MatchOpts(pair_mode=pm.PAREM_PAIR_OFF), length=text.size)
+        assert pm.parem_last_stats()["layout"] == 7
+        assert (off.final_state, off.match_count) == (want.final_state, want.match_count)
+    # carry-in start states through the renumbered variant
+    cut = 1_234_567
+    whole = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, plain)
+    _, va = device_text(torch, plain[:cut], 0)
+    _, vb = device_text(torch, plain[cut:], 0)
+    a = pm.parem_match(dfa, va, length=cut)
+    b = pm.parem_match_ex(dfa, vb, None, pm.MatchOpts(start_state=a.final_state), length=plain.size - cut)
+    assert (b.final_state, a.match_count + b.match_count) == (whole.final_state, whole.match_count)
+    dfa.free()
+
+
+def test_two_byte_stride_variant_declined_when_hot_states_do_not_cover(torch):
+    # 200 short keywords: the 127 most visited states leave most 16-byte vectors to the byte
+    # loop, so the learning step keeps layout 7 (and the results are the oracle's either way)
+    spec = _pair_spec(200, 9)
+    dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    text = wl.zipf_words_text(6 << 20, seed_words=3, seed_plants=4, plant_rate=1e-4, keywords=spec.meta["keywords"])
+    _, view = device_text(torch, text, 0)
+    want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text, want_positions=False)
+    for _ in range(2):
+        got = pm.parem_match_ex(dfa, view, None, pm.MatchOpts(pair_mode=pm.PAREM_PAIR_LEARN), length=text.size)
+        assert (got.final_state, got.match_count) == (want.final_state, want.match_count)
+        assert pm.parem_last_stats()["layout"] == 7
+    assert pm.parem_dfa_get_info(dfa).pair_hot_states == 0
+    dfa.free()
