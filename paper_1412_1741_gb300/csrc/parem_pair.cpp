@@ -79,6 +79,9 @@ Prepared permute(const Prepared& P, const std::vector<uint32_t>& pi) {
 // Largest prepared table (class table and pair table) for which pass 1 still runs enough warps
 // per SM to cover the shared-memory latency of the lookups.
 constexpr uint64_t kPairSmemCap = 172u << 10;
+// Escape bytes after the last row of the pair table (see its construction).
+constexpr uint64_t kPairPad = 144;
+static_assert(27 * 31 + 31 - kPairRow < kPairPad, "pair table padding");
 // Share of 32-lane vector steps allowed to need the byte loop (estimated on the sample).
 constexpr double kPairMaxWarpSlow = 0.4;
 
@@ -123,7 +126,8 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
   std::iota(order.begin(), order.end(), 0u);
   std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return visits[a] > visits[b]; });
   const uint64_t main_bytes = (P.table_bytes + 15) & ~15ull;
-  const uint64_t fit = main_bytes + kPairRow * 2 <= kPairSmemCap ? (kPairSmemCap - main_bytes) / kPairRow - 1 : 0;
+  const uint64_t room = kPairSmemCap - std::min<uint64_t>(kPairSmemCap, main_bytes + kPairPad);
+  const uint64_t fit = room >= 2 * kPairRow ? room / kPairRow - 1 : 0;
   uint32_t H = (uint32_t)std::min<uint64_t>({kPairMaxHot, (uint64_t)k_live, fit});
   while (H > 0 && visits[order[H - 1]] == 0) --H;
   if (H < 2) return give_up(PAREM_OK);
@@ -131,8 +135,10 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
   std::iota(pi.begin(), pi.end(), 0u);
   for (uint32_t i = 0; i < k_live; ++i) pi[order[i]] = i;
   Prepared Q = permute(P, pi);
-  // the pair table: rows 0 .. H-1 for the hot states, row H all escape
-  std::vector<uint8_t> t2((uint64_t)(H + 1) * kPairRow, (uint8_t)H);
+  // the pair table: rows 0 .. H-1 for the hot states, row H all escape, then kPairPad escape
+  // bytes: a vector with a byte outside the set has codes up to 31 (index up to 27*31 + 31 =
+  // 868 inside a row), and its lookups must still read entries <= H, inside the table
+  std::vector<uint8_t> t2((uint64_t)(H + 1) * kPairRow + kPairPad, (uint8_t)H);
   for (uint32_t e = 0; e < H; ++e)
     for (uint32_t f0 = 0; f0 < kPairCodes; ++f0) {
       const uint32_t y = step(Q, e, code_byte(f0));
