@@ -298,6 +298,40 @@ int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, uint64_t len,
                         uint64_t capacity, void* stream, parem_result* out);
 
 /*
+ * parem_pair_preview -- host-only look at the two-byte stride variant (table layout 8) that
+ * scans learn for a DFA with computed columns (layout 7); needs no GPU.
+ *
+ * The paper's candidate runs take one table lookup per symbol.  For texts of lowercase
+ * letters and spaces the library also keeps, for the H states a run visits most (the hot
+ * states, learned from a sample of the first large text), a table of the state reached after
+ * two bytes: byte codes f = b & 0x1F (0 for the space 0x20, 1..26 for a..z), pair index
+ * 27 f0 + f1, entry = hot index of the state after both bytes, or H ("escape") when the
+ * state after either byte is accepting or the state after both is not hot.  Row H is all H.
+ * The main run takes a 16-byte vector two bytes per lookup when it starts in a hot state,
+ * holds only such bytes and never escapes; otherwise it runs the vector byte by byte.
+ * This call plans the variant from `sample` exactly as a scan would and reports it:
+ *   sample       host text, sample_len bytes (one window; the first 64 bytes only settle).
+ *   info         receives the base layout, H, whether the variant pays (a scan would keep it)
+ *                and the estimated share of 32-lane vector steps needing the byte loop.
+ *   hot_states   optional, H uint32: original id of hot state e (the row order).
+ *   pair_table   optional, (H + 1) * 729 bytes (info->pair_table_bytes): the rows.
+ * Errors: INVALID_ARG (as parem_load_dfa), CAPACITY (pair_table_cap too small).
+ */
+typedef struct {
+  uint32_t layout;            /* layout the DFA prepares to (the variant needs 7) */
+  uint32_t hot_states;        /* H, 0 when no variant can be planned */
+  uint32_t accepted;          /* 1: a scan would use the variant */
+  uint32_t reserved;
+  double warp_slow_share;     /* estimated share of 32-lane vector steps needing the byte loop */
+  uint64_t pair_table_bytes;  /* (H + 1) * 729 */
+} parem_pair_info;
+
+int parem_pair_preview(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                       const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                       const uint8_t* sample, uint64_t sample_len, parem_pair_info* info,
+                       uint32_t* hot_states, uint8_t* pair_table, uint64_t pair_table_cap);
+
+/*
  * Batched matching: many (text, DFA) pairs in one persistent launch.
  *
  * The batch is planned once (parem_batch_create) and run any number of times

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "PAREM_NONE", "PAREM_NONE16", "ParemError", "MatchResult", "DfaInfo", "Dfa", "MatchOpts",
-    "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa",
+    "load_library", "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_pair_preview",
     "parem_match", "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror",
     "parem_version", "parem_last_stats", "parem_match_noalloc", "Stats", "EXPORTED_SYMBOLS",
     "PAREM_ERR_TOO_LARGE", "PAREM_NOALLOC_SCRATCH_BYTES", "parem_batch_create", "Batch", "BatchOpts",
@@ -45,7 +45,7 @@ _LIB = None
 
 # Every symbol declared in include/parem.h.
 EXPORTED_SYMBOLS = [
-    "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_match",
+    "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_pair_preview", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
     "parem_last_stats", "parem_match_noalloc", "parem_batch_create", "parem_batch_run", "parem_batch_results",
     "parem_batch_item_segment", "parem_batch_stats", "parem_batch_free", "parem_server_create", "parem_server_submit",
@@ -229,6 +229,49 @@ def _info(i: _Info) -> DfaInfo:
                    i.pair_hot_states)
 
 
+class _PairInfo(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_uint32), ("hot_states", ctypes.c_uint32), ("accepted", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("warp_slow_share", ctypes.c_double),
+                ("pair_table_bytes", ctypes.c_uint64)]
+
+
+@dataclass
+class PairPreview:
+    layout: int
+    hot_states: int
+    accepted: bool
+    warp_slow_share: float
+    hot_orig: np.ndarray      # original id of each hot state (row order)
+    pair_table: np.ndarray    # (hot_states + 1) x 729 uint8
+
+
+def parem_pair_preview(table, byte_to_symbol, start, accept, sample) -> PairPreview:
+    """Host-only plan of the two-byte stride variant for this DFA and text sample (no GPU)."""
+    lib = load_library()
+    table, b2s, accept = _dfa_arrays(table, byte_to_symbol, accept)
+    sample = np.ascontiguousarray(sample, dtype=np.uint8)
+    info = _PairInfo()
+    vp = ctypes.c_void_p
+    lib.parem_pair_preview.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint32, vp, ctypes.c_uint32, vp, vp,
+                                       ctypes.c_uint64, ctypes.POINTER(_PairInfo), vp, vp, ctypes.c_uint64]
+    lib.parem_pair_preview.restype = ctypes.c_int
+    args = (table.ctypes.data, table.shape[0], table.shape[1], None if b2s is None else b2s.ctypes.data,
+            int(start), accept.ctypes.data, sample.ctypes.data, int(sample.size))
+    rc = lib.parem_pair_preview(*args, ctypes.byref(info), None, None, ctypes.c_uint64(0))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_pair_preview")
+    hot = np.zeros(max(info.hot_states, 1), np.uint32)
+    t2 = np.zeros(max(int(info.pair_table_bytes), 1), np.uint8)
+    if info.hot_states:
+        rc = lib.parem_pair_preview(*args, ctypes.byref(info), hot.ctypes.data, t2.ctypes.data,
+                                    ctypes.c_uint64(t2.size))
+        if rc != PAREM_OK:
+            raise ParemError(rc, "parem_pair_preview")
+    return PairPreview(info.layout, info.hot_states, bool(info.accepted), info.warp_slow_share,
+                       hot[:info.hot_states], t2[:int(info.pair_table_bytes)].reshape(-1, 729) if info.hot_states
+                       else np.zeros((0, 729), np.uint8))
+
+
 def parem_prepare_info(table, byte_to_symbol, start, accept) -> DfaInfo:
     lib = load_library()
     table, b2s, accept = _dfa_arrays(table, byte_to_symbol, accept)
@@ -301,7 +344,13 @@ def parem_load_regex(pattern, flags: int = 0, max_states: int = 0) -> Dfa:
 
 
 def parem_dfa_get_info(dfa: Dfa) -> DfaInfo:
-    return dfa.info
+    """The DFA's description as the library reports it now (the two-byte stride variant's hot
+    states appear once a scan has learned them)."""
+    info = _Info()
+    rc = load_library().parem_dfa_get_info(dfa.handle, ctypes.byref(info))
+    if rc != PAREM_OK:
+        raise ParemError(rc, "parem_dfa_get_info")
+    return _info(info)
 
 
 def parem_free_dfa(dfa: Dfa) -> None:

@@ -64,8 +64,19 @@ void learn_convergence(const parem_dfa* dfa, uint32_t spec_cap, uint32_t nonconv
 constexpr uint32_t kPairNone = 0, kPairBusy = 1, kPairReady = 2, kPairOff = 3;
 // Texts at least this long teach a kClassWin DFA its hot states (parem_pair.cpp).
 constexpr uint64_t kPairLearnBytes = 64ull << 20;
-// Sample the device text, choose the hot states, build and upload the kClassPair variant when
-// it pays (parem_pair.cpp); sets pair_state to kPairReady or kPairOff.  Host call, blocking.
+// The kClassPair variant of a kClassWin DFA planned from a host text sample (nwin windows of
+// wlen bytes): hot states, the renumbered copy with its pair table, and the estimated share
+// of 32-lane vector steps that would need the byte loop (parem_pair.cpp).
+struct PairPlan {
+  bool ok = false;               // worth using (the share is small enough)
+  uint32_t hot = 0;              // hot states H (0: no variant)
+  double warp_slow = 1.0;
+  std::vector<uint32_t> hot_orig;  // original id of hot state e
+  Prepared Q;
+};
+int plan_pairs(const Prepared& P, const uint8_t* sample, uint64_t nwin, uint64_t wlen, PairPlan* out);
+// Sample the device text, plan the variant and upload it when it pays; sets pair_state to
+// kPairReady or kPairOff.  Host call, blocking.
 int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t stream);
 // The device copy of a prepared DFA: one allocation (table, column map, byte classes,
 // candidate lists, ranks) and the DeviceDfa that points into it (parem_api.cu).

@@ -87,34 +87,19 @@ constexpr double kPairMaxWarpSlow = 0.4;
 
 }  // namespace
 
-int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t stream) {
-  const Prepared& P = dfa->host;
-  auto give_up = [&](int rc) {
-    dfa->pair_state.store(kPairOff, std::memory_order_release);
-    return rc;
-  };
+int plan_pairs(const Prepared& P, const uint8_t* sample, uint64_t nwin, uint64_t wlen, PairPlan* out) {
+  out->ok = false;
+  out->hot = 0;
+  out->warp_slow = 1.0;
   const uint32_t k_live = P.first_accept - P.has_dead;  // non-accepting live states: 0 .. k-1
-  if (P.layout != kClassWin || k_live < 2) return give_up(PAREM_OK);
-  // sample: up to 64 windows of 64 KiB spread over the text (the whole text when short)
-  uint64_t nwin = 64, wlen = std::min<uint64_t>(64u << 10, len / 64) & ~15ull;
-  if (wlen < 4096) {
-    nwin = 1;
-    wlen = std::min<uint64_t>(len, 4u << 20);
-  }
-  std::vector<uint8_t> buf(nwin * wlen);
-  for (uint64_t k = 0; k < nwin; ++k) {
-    const uint64_t off = nwin == 1 ? 0 : (len - wlen) / (nwin - 1) * k;
-    if (cudaMemcpyAsync(buf.data() + k * wlen, text + off, wlen, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-      return give_up(PAREM_ERR_CUDA);
-  }
-  if (cudaStreamSynchronize(stream) != cudaSuccess) return give_up(PAREM_ERR_CUDA);
+  if (P.layout != kClassWin || k_live < 2 || nwin == 0 || wlen < 16) return PAREM_OK;
   // visits per state, from the start state in every window (the first 64 bytes only settle
   // the run onto the text's states and are not counted)
   const uint64_t settle = std::min<uint64_t>(64, wlen / 4);
   std::vector<uint64_t> visits(P.n, 0);
   for (uint64_t k = 0; k < nwin; ++k) {
     uint32_t s = P.start;
-    const uint8_t* w = buf.data() + k * wlen;
+    const uint8_t* w = sample + k * wlen;
     for (uint64_t j = 0; j < wlen; ++j) {
       s = step(P, s, w[j]);
       if (j >= settle) ++visits[s];
@@ -130,7 +115,7 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
   const uint64_t fit = room >= 2 * kPairRow ? room / kPairRow - 1 : 0;
   uint32_t H = (uint32_t)std::min<uint64_t>({kPairMaxHot, (uint64_t)k_live, fit});
   while (H > 0 && visits[order[H - 1]] == 0) --H;
-  if (H < 2) return give_up(PAREM_OK);
+  if (H < 2) return PAREM_OK;
   std::vector<uint32_t> pi(P.n);
   std::iota(pi.begin(), pi.end(), 0u);
   for (uint32_t i = 0; i < k_live; ++i) pi[order[i]] = i;
@@ -152,7 +137,7 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
   uint64_t vec = 0, slow = 0;
   for (uint64_t k = 0; k < nwin; ++k) {
     uint32_t s = Q.start;
-    const uint8_t* w = buf.data() + k * wlen;
+    const uint8_t* w = sample + k * wlen;
     for (uint64_t j = 0; j + 16 <= wlen; j += 16) {
       bool fast = s < H;
       uint32_t e = std::min(s, H);
@@ -170,7 +155,10 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
     }
   }
   const double p_slow = vec ? (double)slow / (double)vec : 1.0;
-  if (1.0 - std::pow(1.0 - p_slow, 32.0) > kPairMaxWarpSlow) return give_up(PAREM_OK);
+  out->warp_slow = 1.0 - std::pow(1.0 - p_slow, 32.0);
+  out->hot = H;
+  out->hot_orig.resize(H);
+  for (uint32_t e = 0; e < H; ++e) out->hot_orig[e] = Q.orig_of[e];
   Q.layout = kClassPair;
   Q.pair_hot = H;
   Q.main_bytes = (uint32_t)main_bytes;
@@ -178,11 +166,38 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
   Q.table.resize(main_bytes + ((t2.size() + 15) & ~(size_t)15), 0);
   std::memcpy(Q.table.data() + main_bytes, t2.data(), t2.size());
   Q.table_bytes = (uint32_t)Q.table.size();
+  out->Q = std::move(Q);
+  out->ok = out->warp_slow <= kPairMaxWarpSlow;
+  return PAREM_OK;
+}
+
+int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t stream) {
+  auto give_up = [&](int rc) {
+    dfa->pair_state.store(kPairOff, std::memory_order_release);
+    return rc;
+  };
+  if (dfa->host.layout != kClassWin) return give_up(PAREM_OK);
+  // sample: up to 64 windows of 64 KiB spread over the text (the whole text when short)
+  uint64_t nwin = 64, wlen = std::min<uint64_t>(64u << 10, len / 64) & ~15ull;
+  if (wlen < 4096) {
+    nwin = 1;
+    wlen = std::min<uint64_t>(len, 4u << 20);
+  }
+  std::vector<uint8_t> buf(nwin * wlen);
+  for (uint64_t k = 0; k < nwin; ++k) {
+    const uint64_t off = nwin == 1 ? 0 : (len - wlen) / (nwin - 1) * k;
+    if (cudaMemcpyAsync(buf.data() + k * wlen, text + off, wlen, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+      return give_up(PAREM_ERR_CUDA);
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return give_up(PAREM_ERR_CUDA);
+  PairPlan pp;
+  plan_pairs(dfa->host, buf.data(), nwin, wlen, &pp);
+  if (!pp.ok) return give_up(PAREM_OK);
   DeviceDfa D{};
   void* mem = nullptr;
-  const int rc = upload_prepared(Q, &D, &mem);
+  const int rc = upload_prepared(pp.Q, &D, &mem);
   if (rc != PAREM_OK) return give_up(rc);
-  dfa->pair_host = std::move(Q);
+  dfa->pair_host = std::move(pp.Q);
   dfa->pair_dev = D;
   dfa->pair_mem = mem;
   dfa->pair_state.store(kPairReady, std::memory_order_release);
@@ -190,3 +205,30 @@ int learn_pairs(parem_dfa* dfa, const uint8_t* text, uint64_t len, cudaStream_t 
 }
 
 }  // namespace parem
+
+// Host-only preview of the pair variant (no GPU): see include/parem.h.
+extern "C" int parem_pair_preview(const uint32_t* table, uint32_t n_states, uint32_t n_symbols,
+                                  const uint16_t* byte_to_symbol, uint32_t start, const uint8_t* accept,
+                                  const uint8_t* sample, uint64_t sample_len, parem_pair_info* info,
+                                  uint32_t* hot_states, uint8_t* pair_table, uint64_t pair_table_cap) {
+  if (!info || (sample_len > 0 && !sample)) return PAREM_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  parem::Prepared P;
+  int rc = parem::prepare_dfa(table, n_states, n_symbols, byte_to_symbol, start, accept, 160u << 10, &P);
+  if (rc != PAREM_OK) return rc;
+  info->layout = P.layout;
+  parem::PairPlan pp;
+  parem::plan_pairs(P, sample, 1, sample_len, &pp);
+  info->hot_states = pp.hot;
+  info->accepted = pp.ok ? 1u : 0u;
+  info->warp_slow_share = pp.warp_slow;
+  if (pp.hot == 0) return PAREM_OK;
+  info->pair_table_bytes = (uint64_t)(pp.hot + 1) * parem::kPairRow;
+  if (hot_states)
+    for (uint32_t e = 0; e < pp.hot; ++e) hot_states[e] = pp.hot_orig[e];
+  if (pair_table) {
+    if (pair_table_cap < info->pair_table_bytes) return PAREM_ERR_CAPACITY;
+    std::memcpy(pair_table, pp.Q.table.data() + pp.Q.pair_off, info->pair_table_bytes);
+  }
+  return PAREM_OK;
+}

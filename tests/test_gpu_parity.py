@@ -476,23 +476,23 @@ def test_text_longer_than_4gib_against_the_oracle(torch):
     assert np.array_equal(hpos, want.positions)
 
 
-def _pair_spec(n_keywords=64, seed=1):
-    if n_keywords == 64 and seed == 1:
+def _pair_spec(n_keywords=64, seed=1, lo=8, hi=24):
+    if (n_keywords, seed, lo, hi) == (64, 1, 8, 24):
         return AC
-    kws = wl.random_keywords(n_keywords, 3, 10, seed=seed)
+    kws = wl.random_keywords(n_keywords, lo, hi, seed=seed)
     sym = wl.letters_byte_map()
     t, acc = wl.aho_corasick_dfa([[int(sym[b]) for b in kw] for kw in kws], 27)
     return wl.DfaSpec(t, 0, acc, sym, f"ac{n_keywords}-{seed}", {"keywords": kws})
 
 
-@pytest.mark.parametrize("n_keywords,seed", [(64, 1), (12, 5), (40, 9)])
-def test_two_byte_stride_variant(torch, n_keywords, seed):
+@pytest.mark.parametrize("n_keywords,seed,lo,hi", [(64, 1, 8, 24), (48, 7, 6, 16), (96, 13, 8, 20)])
+def test_two_byte_stride_variant(torch, n_keywords, seed, lo, hi):
     # The two-byte stride variant (layout 8) of a computed-column keyword DFA, learned from the
     # first text: scans that use it give the oracle's result on texts of letters and spaces,
     # texts with every other kind of byte sprinkled in (each sends its vector to the byte loop),
     # texts dense with keywords (escapes through accepting states), carry-in starts, capacity
     # limits, count-only calls and forced row lengths.
-    spec = _pair_spec(n_keywords, seed)
+    spec = _pair_spec(n_keywords, seed, lo, hi)
     kws = spec.meta["keywords"]
     dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
     assert pm.parem_dfa_get_info(dfa).layout == 7
@@ -549,7 +549,7 @@ def test_two_byte_stride_variant(torch, n_keywords, seed):
 def test_two_byte_stride_variant_declined_when_hot_states_do_not_cover(torch):
     # 200 short keywords: the 127 most visited states leave most 16-byte vectors to the byte
     # loop, so the learning step keeps layout 7 (and the results are the oracle's either way)
-    spec = _pair_spec(200, 9)
+    spec = _pair_spec(200, 9, 3, 10)
     dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
     text = wl.zipf_words_text(6 << 20, seed_words=3, seed_plants=4, plant_rate=1e-4, keywords=spec.meta["keywords"])
     _, view = device_text(torch, text, 0)
