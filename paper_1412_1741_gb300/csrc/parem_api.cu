@@ -102,15 +102,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-int encode_rows(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R) {
+// Tensor map of R rows of S bytes: boxes of `box` bytes (32 or 64) x 32 rows, swizzled by the
+// box width so that the 32 lanes' 16-byte reads of one chunk fall in distinct banks.
+int encode_rows(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R, uint32_t box_w = kBox) {
   auto fn = encode_fn();
   if (!fn) return PAREM_ERR_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)S, (cuuint64_t)R};
   cuuint64_t strides[1] = {(cuuint64_t)S};
-  cuuint32_t box[2] = {kBox, kLanes};
+  cuuint32_t box[2] = {box_w, kLanes};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(base), dims, strides, box,
-                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, box_w == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? PAREM_OK : PAREM_ERR_CUDA;
 }
@@ -442,7 +444,7 @@ int plan_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, const par
   if (pl->P > 1 && P.n <= 16384 && (m_need > 32u * pl->P || (P.sync_len > kBitmapSync && P.n >= 256)))
     pl->bitmap_words = (P.n + 31) / 32;
   pl->spec_bytes = kSpecBytes + (pl->bitmap_words ? (uint32_t)round_up(8ull * pl->bitmap_words, 16) + 512u : 0u);
-  const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + pl->spec_bytes;
+  const uint32_t per_warp = kStages * kLanes * box_bytes(P.layout) + kStages * 8 + pl->spec_bytes;
   int warps = (int)((props.smem_optin - (int)fixed) / (int)per_warp);
   // the launch bounds of the kernel variants
   warps = std::min(warps, P.layout == kClassPair ? (int)kPairMaxWarps : pl->P >= 4 ? 24 : 32);
@@ -644,15 +646,18 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   if (pl.R == 0) {
     e = launch_tiny_dispatch(P.layout, P.esize, p, small_smem, stream);
   } else {
-    CUtensorMap tm;
-    rc = encode_rows(&tm, text + pl.h, pl.S, pl.R);
+    // pass 1 reads boxes of box_bytes(layout); the streaming emit pass always 64-byte boxes
+    CUtensorMap tm, tm_emit;
+    rc = encode_rows(&tm, text + pl.h, pl.S, pl.R, box_bytes(P.layout));
+    if (rc == PAREM_OK && box_bytes(P.layout) != kBox) rc = encode_rows(&tm_emit, text + pl.h, pl.S, pl.R);
     if (rc != PAREM_OK) return rc;
+    if (box_bytes(P.layout) == kBox) tm_emit = tm;
     e = launch_scan_dispatch(P.layout, P.esize, pl.P, tm, p, pl.grid, pl.warps * 32, pl.smem, stream);
     if (e == cudaSuccess && timed) e = cudaEventRecord(sc->ev[1], stream);
     if (e == cudaSuccess && emit) {
       sc->emitted = true;
       const DevProps props = dev_props(dfa->device);
-      e = launch_emit_dispatch(P.layout, P.esize, p, &tm, props.sms, 256, small_smem, stream);
+      e = launch_emit_dispatch(P.layout, P.esize, p, &tm_emit, props.sms, 256, small_smem, stream);
     }
   }
   if (e == cudaSuccess && timed && pl.R == 0) e = cudaEventRecord(sc->ev[1], stream);

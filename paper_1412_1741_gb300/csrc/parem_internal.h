@@ -49,7 +49,10 @@ enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClass
 constexpr uint32_t kPairCodes = 27;
 constexpr uint32_t kPairRow = kPairCodes * kPairCodes;  // 729 entries per row
 constexpr uint32_t kPairMaxHot = 127;
-constexpr uint32_t kPairMaxWarps = 16;  // warps per block of its pass 1 (its tables leave no room for more)
+constexpr uint32_t kPairMaxWarps = 24;  // warps per block of its pass 1 (registers and shared memory)
+// Text box of pass 1's TMA stages per row: 32 bytes (32-byte swizzle) for kClassPair, whose
+// tables leave less shared memory for stages, 64 bytes (64-byte swizzle) otherwise.
+constexpr uint32_t box_bytes(uint32_t layout) { return layout == kClassPair ? 32u : kBox; }
 constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
 // Shared memory of every kernel starts with the column map (512 B reserved) followed by the
 // table at this fixed offset, so table reads use an immediate offset.

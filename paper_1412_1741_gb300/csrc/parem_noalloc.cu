@@ -45,7 +45,7 @@ int scratch_address(int dev, void** out) {
   return PAREM_OK;
 }
 
-int encode_rows_noalloc(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R) {
+int encode_rows_noalloc(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64_t R, uint32_t box_w) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -59,10 +59,11 @@ int encode_rows_noalloc(CUtensorMap* tm, const uint8_t* base, uint64_t S, uint64
   if (!fn) return PAREM_ERR_CUDA;
   cuuint64_t dims[2] = {(cuuint64_t)S, (cuuint64_t)R};
   cuuint64_t strides[1] = {(cuuint64_t)S};
-  cuuint32_t box[2] = {kBox, kLanes};
+  cuuint32_t box[2] = {box_w, kLanes};
   cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(base), dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        box_w == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? PAREM_OK : PAREM_ERR_CUDA;
 }
@@ -147,14 +148,16 @@ extern "C" int parem_match_noalloc(const parem_dfa* dfa, const uint8_t* text, ui
   if (pl.R == 0) {
     e = launch_tiny_dispatch(P.layout, P.esize, p, small_smem, st);
   } else {
-    CUtensorMap tm;
-    rc = encode_rows_noalloc(&tm, text + pl.h, pl.S, pl.R);
+    // pass 1 reads boxes of box_bytes(layout); the streaming emit pass always 64-byte boxes
+    CUtensorMap tm, tm_emit;
+    rc = encode_rows_noalloc(&tm, text + pl.h, pl.S, pl.R, box_bytes(P.layout));
+    if (rc == PAREM_OK) rc = encode_rows_noalloc(&tm_emit, text + pl.h, pl.S, pl.R, kBox);
     if (rc != PAREM_OK) return rc;
     e = launch_scan_dispatch(P.layout, P.esize, pl.P, tm, p, pl.grid, pl.warps * 32, pl.smem, st);
     if (e == cudaSuccess && emit) {
       int sms = 0;
       if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAREM_ERR_CUDA;
-      e = launch_emit_dispatch(P.layout, P.esize, p, &tm, sms, 256, small_smem, st);
+      e = launch_emit_dispatch(P.layout, P.esize, p, &tm_emit, sms, 256, small_smem, st);
     }
   }
   if (e != cudaSuccess) return PAREM_ERR_CUDA;

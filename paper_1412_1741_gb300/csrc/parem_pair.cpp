@@ -76,9 +76,10 @@ Prepared permute(const Prepared& P, const std::vector<uint32_t>& pi) {
   return Q;
 }
 
-// Largest prepared table (class table and pair table) for which pass 1 still runs enough warps
-// per SM to cover the shared-memory latency of the lookups.
-constexpr uint64_t kPairSmemCap = 172u << 10;
+// Largest prepared table (class table and pair table): pass 1 then still runs kPairMaxWarps
+// warps per block (2,752 bytes of stages, barriers and speculation scratch each) in the
+// 227 KiB of shared memory a block may have, to cover the latency of the dependent lookups.
+constexpr uint64_t kPairSmemCap = 160u << 10;
 // Escape bytes after the last row of the pair table (see its construction).
 constexpr uint64_t kPairPad = 144;
 static_assert(27 * 31 + 31 - kPairRow < kPairPad, "pair table padding");

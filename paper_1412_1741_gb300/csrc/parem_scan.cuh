@@ -408,7 +408,11 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   const DeviceDfa& D = p.dfa;
   const uint32_t dead = D.dead;  // kEmpty when the DFA has no dead state
   const uint32_t A = D.first_accept;
-  const uint32_t nblk = (uint32_t)(p.S / kBox);
+  // the row's bytes arrive in boxes of BOX bytes (32 rows x BOX per stage), swizzled in
+  // 16-byte chunks by the TMA unit: chunk c of row k sits at c ^ ((k / SWZ_DIV) & SWZ_MASK)
+  constexpr uint32_t BOX = box_bytes(LAYOUT), SB = kLanes * BOX;
+  constexpr uint32_t SWZ_DIV = 128u / BOX, SWZ_MASK = BOX / 16u - 1u;
+  const uint32_t nblk = (uint32_t)(p.S / BOX);
   const uint32_t issue_first = nblk < kStages ? nblk : kStages;
   const uint32_t cap = p.spec_cap;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -427,9 +431,8 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   if (lane == 0) {
     for (uint32_t b = 0; b < issue_first; ++b) {
       const uint32_t bar = smem_u32(sm + bar0 + 8 * b);
-      mbar_arrive_expect_tx(bar, kStageBytes);
-      tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), tmap, bar, (int32_t)(b * kBox),
-                  (int32_t)row0);
+      mbar_arrive_expect_tx(bar, SB);
+      tma_load_2d(smem_u32(sm + stage0 + b * SB), tmap, bar, (int32_t)(b * BOX), (int32_t)row0);
     }
   }
   pending |= (1u << issue_first) - 1u;
@@ -441,11 +444,11 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
   }
   // the first bytes of every row of the chunk are already staged in shared memory
-  const uint32_t staged = issue_first * kBox;
+  const uint32_t staged = issue_first * BOX;
   auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 {
-    const uint32_t b = pos / kBox;
-    const uint32_t ch = ((pos % kBox) / 16u) ^ ((k >> 1) & 3u);
-    return *reinterpret_cast<const uint4*>(sm + stage0 + b * kStageBytes + k * kBox + ch * 16u);
+    const uint32_t b = pos / BOX;
+    const uint32_t ch = ((pos % BOX) / 16u) ^ ((k / SWZ_DIV) & SWZ_MASK);
+    return *reinterpret_cast<const uint4*>(sm + stage0 + b * SB + k * BOX + ch * 16u);
   };
   auto cand_class = [&](uint64_t r) -> uint32_t {
     return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
@@ -997,25 +1000,24 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
     phase_bits ^= 1u << b;
     pending &= ~(1u << b);
-    uint4 v[kBox / 16];
-    const uint8_t* stg = sm + stage0 + b * kStageBytes + lane * kBox;
+    uint4 v[BOX / 16];
+    const uint8_t* stg = sm + stage0 + b * SB + lane * BOX;
 #pragma unroll
-    for (uint32_t i = 0; i < kBox / 16; ++i)
-      v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane >> 1) & 3u)) * 16u));
+    for (uint32_t i = 0; i < BOX / 16; ++i)
+      v[i] = *reinterpret_cast<const uint4*>(stg + ((i ^ ((lane / SWZ_DIV) & SWZ_MASK)) * 16u));
     __syncwarp();
     if (blk + kStages < nblk) {
       if (lane == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, kStageBytes);
-        tma_load_2d(smem_u32(sm + stage0 + b * kStageBytes), tmap, bar,
-                    (int32_t)((blk + kStages) * kBox), (int32_t)row0);
+        mbar_arrive_expect_tx(bar, SB);
+        tma_load_2d(smem_u32(sm + stage0 + b * SB), tmap, bar, (int32_t)((blk + kStages) * BOX), (int32_t)row0);
       }
       pending |= 1u << b;
     }
     if (run) {
-      const uint32_t col0 = blk * kBox;
+      const uint32_t col0 = blk * BOX;
 #pragma unroll
-      for (uint32_t i = 0; i < kBox / 16; ++i) {
+      for (uint32_t i = 0; i < BOX / 16; ++i) {
         const uint32_t col = col0 + i * 16u;
         if (col >= my_t) {
           bool exact = true;  // the vector is run byte by byte below
@@ -1039,8 +1041,11 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
               acc_a |= (f + 0x3F3F3F3Fu) ^ w;  // bit 7: b >= 0x80; bit 6: bit 6 of b != (f != 0)
               acc_b |= f + 0x65656565u;        // bit 7: f >= 27
               acc_c &= w;                      // bit 5 must stay set
-              e = sm[kTableOff + __dp4a(f, 0x0000011Bu, e * kPairRow + t2)];
-              e = sm[kTableOff + __dp4a(f, 0x011B0000u, e * kPairRow + t2)];
+              // the pair offsets do not depend on the state: only one multiply-add and the
+              // lookup are on the dependent chain
+              const uint32_t q01 = __dp4a(f, 0x0000011Bu, t2), q23 = __dp4a(f, 0x011B0000u, t2);
+              e = sm[kTableOff + e * kPairRow + q01];
+              e = sm[kTableOff + e * kPairRow + q23];
             }
             const uint32_t bad = (acc_a & 0xC0C0C0C0u) | (acc_b & 0x80808080u) | (~acc_c & 0x20202020u);
             if (bad == 0u && e < H) {
@@ -1488,12 +1493,13 @@ __global__ void __launch_bounds__(spec_scan_threads<LAYOUT, P>(), 1)
   clear_prev_header(p);
   load_tables<LAYOUT, ESIZE>(sm, p.dfa);
   const uint32_t region = stage_region_off(smem_raw, Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes);
+  constexpr uint32_t SB = kLanes * box_bytes(LAYOUT);  // bytes of one stage
   WarpCtx wc;
   wc.sm = sm;
   wc.lane = lane;
-  wc.stage0 = region + warp * (kStages * kStageBytes);
-  wc.bar0 = region + nwarps * (kStages * kStageBytes) + warp * (kStages * 8);
-  const uint32_t spec0 = region + nwarps * (kStages * kStageBytes + kStages * 8) + warp * p.spec_bytes;
+  wc.stage0 = region + warp * (kStages * SB);
+  wc.bar0 = region + nwarps * (kStages * SB) + warp * (kStages * 8);
+  const uint32_t spec0 = region + nwarps * (kStages * SB + kStages * 8) + warp * p.spec_bytes;
   wc.hand = reinterpret_cast<uint16_t*>(sm + spec0);
   wc.cbuf = reinterpret_cast<uint32_t*>(sm + spec0 + kLanes * kLaneCand * 2);
   // 2 x bitmap_words words of candidate bitmaps, then a list of up to 256 states
