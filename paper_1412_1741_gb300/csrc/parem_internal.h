@@ -45,10 +45,10 @@ enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClass
 // The hot states are the compact states 0 .. H-1 (non-accepting, the most visited ones); row
 // e < H holds, for every pair, the hot state reached after both bytes, or the escape value H
 // when an intermediate or final state is accepting or not hot.  Row H is all H, so an escaped
-// run stays escaped.  Entries are bytes; H <= 127.
+// run stays escaped.  Entries are bytes; H <= 254 (in practice shared memory bounds H).
 constexpr uint32_t kPairCodes = 27;
 constexpr uint32_t kPairRow = kPairCodes * kPairCodes;  // 729 entries per row
-constexpr uint32_t kPairMaxHot = 127;
+constexpr uint32_t kPairMaxHot = 254;
 constexpr uint32_t kPairMaxWarps = 24;  // warps per block of its pass 1 (registers and shared memory)
 // Text box of pass 1's TMA stages per row: 32 bytes (32-byte swizzle) for kClassPair, whose
 // tables leave less shared memory for stages, 64 bytes (64-byte swizzle) otherwise.

@@ -106,7 +106,7 @@ int plan_pairs(const Prepared& P, const uint8_t* sample, uint64_t nwin, uint64_t
       if (j >= settle) ++visits[s];
     }
   }
-  // hot states: the most visited non-accepting live states (ties by id), at most 127 and as
+  // hot states: the most visited non-accepting live states (ties by id), at most 254 and as
   // many as fit the shared-memory cap next to the class table
   std::vector<uint32_t> order(k_live);
   std::iota(order.begin(), order.end(), 0u);

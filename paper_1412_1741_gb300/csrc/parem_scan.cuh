@@ -1035,23 +1035,26 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
             uint32_t e = min(s, H);
             uint32_t acc_a = 0, acc_b = 0, acc_c = 0xFFFFFFFFu;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const uint32_t w = ws[g];
-              const uint32_t f = w & 0x1F1F1F1Fu;
-              acc_a |= (f + 0x3F3F3F3Fu) ^ w;  // bit 7: b >= 0x80; bit 6: bit 6 of b != (f != 0)
-              acc_b |= f + 0x65656565u;        // bit 7: f >= 27
-              acc_c &= w;                      // bit 5 must stay set
+            for (int g = 0; g < 4; g += 2) {
+              const uint32_t w0 = ws[g], w1 = ws[g + 1];
+              const uint32_t f0 = w0 & 0x1F1F1F1Fu, f1 = w1 & 0x1F1F1F1Fu;
+              // bit 7: b >= 0x80; bit 6: bit 6 of b != (f != 0)
+              acc_a |= (f0 + 0x3F3F3F3Fu) ^ w0;
+              acc_a |= (f1 + 0x3F3F3F3Fu) ^ w1;
+              acc_b |= (f0 + 0x65656565u) | (f1 + 0x65656565u);  // bit 7: f >= 27
+              acc_c &= w0 & w1;                                  // bit 5 must stay set
               // the pair offsets do not depend on the state: only one multiply-add and the
               // lookup are on the dependent chain
-              const uint32_t q01 = __dp4a(f, 0x0000011Bu, t2), q23 = __dp4a(f, 0x011B0000u, t2);
-              e = sm[kTableOff + e * kPairRow + q01];
-              e = sm[kTableOff + e * kPairRow + q23];
+              const uint32_t q0 = __dp4a(f0, 0x0000011Bu, t2), q1 = __dp4a(f0, 0x011B0000u, t2);
+              const uint32_t q2 = __dp4a(f1, 0x0000011Bu, t2), q3 = __dp4a(f1, 0x011B0000u, t2);
+              e = sm[kTableOff + e * kPairRow + q0];
+              e = sm[kTableOff + e * kPairRow + q1];
+              e = sm[kTableOff + e * kPairRow + q2];
+              e = sm[kTableOff + e * kPairRow + q3];
             }
             const uint32_t bad = (acc_a & 0xC0C0C0C0u) | (acc_b & 0x80808080u) | (~acc_c & 0x20202020u);
-            if (bad == 0u && e < H) {
-              s = e;
-              exact = false;
-            }
+            exact = (bad != 0u) | (e >= H);
+            if (!exact) s = e;
           }
           if (exact) {
           const uint32_t mu0 = mu, s0 = s;

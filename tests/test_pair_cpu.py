@@ -36,7 +36,7 @@ def test_pair_table_entries_are_two_oracle_steps(lib, n_keywords, lo, hi, seed):
     spec = wl.keywords_ac_dfa() if seed == 1 else _ac(n_keywords, lo, hi, seed)
     sample = wl.zipf_words_text(1 << 20, seed_words=3, seed_plants=4, plant_rate=1e-4, keywords=spec.meta["keywords"])
     pv = pm.parem_pair_preview(spec.table, spec.byte_to_symbol, spec.start, spec.accept, sample)
-    assert pv.layout == 7 and 2 <= pv.hot_states <= 127
+    assert pv.layout == 7 and 2 <= pv.hot_states <= 254
     H = pv.hot_states
     table = [list(map(int, r)) for r in np.asarray(spec.table)]
     acc = np.asarray(spec.accept).astype(bool)
@@ -85,7 +85,7 @@ def test_pair_preview_declines_where_hot_states_do_not_cover(lib):
     spec = _ac(200, 3, 10, 9)
     sample = wl.zipf_words_text(1 << 20, seed_words=3, seed_plants=4, plant_rate=1e-4, keywords=spec.meta["keywords"])
     pv = pm.parem_pair_preview(spec.table, spec.byte_to_symbol, spec.start, spec.accept, sample)
-    assert pv.layout == 7 and pv.hot_states == 127 and not pv.accepted and pv.warp_slow_share > 0.4
+    assert pv.layout == 7 and pv.hot_states >= 100 and not pv.accepted and pv.warp_slow_share > 0.4
 
 
 def test_pair_preview_needs_computed_columns(lib):
