@@ -1141,21 +1141,43 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   if (failed) return;
   lv = (fv == kEmpty) ? 0u : lvv + 16u;
   if (run && last_row && p.tail) {
+    // the tail after the last full row (16-byte aligned, shorter than a row) is on the critical
+    // path of the scan: it is read 16 bytes at a time with the next vector's load in flight,
+    // and its last partial vector by independent byte loads
     const uint8_t* tp = body + p.R * p.S;
-    for (uint64_t o = 0; o < p.tail; ++o) {
-      const uint32_t s0 = s;
-      s = tab.next(s, tab.col(ldg8(tp + o)));
-      if (s >= A) {
-        ++mu;
-        if (fv == kEmpty) {
-          fv = (uint32_t)(p.S + o);
-          fs = s0;
+    const uint32_t tl = (uint32_t)p.tail;
+    const uint32_t full = tl & ~15u;
+    uint4 nx = full ? ldg16(tp) : make_uint4(0, 0, 0, 0);
+    for (uint32_t o = 0; o < tl; o += 16) {
+      uint4 cur = nx;
+      if (o + 16 < full) nx = ldg16(tp + o + 16);
+      if (o >= full) {  // the last partial vector
+        uint32_t wv[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (uint32_t q = 0; q < 16; ++q)
+          if (o + q < tl) wv[q >> 2] |= ldg8(tp + o + q) << (8 * (q & 3));
+        cur = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      }
+      const uint32_t n_here = min(16u, tl - o);
+#pragma unroll
+      for (uint32_t q = 0; q < 16; ++q) {
+        if (q < n_here) {
+          const uint32_t s0 = s;
+          s = tab.next(s, tab.col(byte_of(cur, (int)q)));
+          if (s >= A) {
+            ++mu;
+            const uint32_t at = (uint32_t)p.S + o + q;
+            if (fv == kEmpty) {
+              fv = at;
+              fs = s0;
+            }
+            lvv = at;
+            ls = s0;
+            lv = lvv + 1;
+            if (myslots != nullptr && nrec < kRowSlots) myslots[nrec] = lvv;
+            ++nrec;
+          }
         }
-        lvv = (uint32_t)(p.S + o);
-        ls = s0;
-        lv = lvv + 1;
-        if (myslots != nullptr && nrec < kRowSlots) myslots[nrec] = lvv;
-        ++nrec;
       }
     }
   }
