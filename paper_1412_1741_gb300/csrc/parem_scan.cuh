@@ -315,6 +315,69 @@ __device__ __forceinline__ unsigned long long pack_status(uint32_t flag, uint32_
          ((unsigned long long)(E & 0xFFFFu) << 45) | (cnt & kCountMask);
 }
 
+// Every chunk's inclusive prefix from the published status words, by one warp: a segmented
+// scan in text order over (dead, count), where a chunk that has already published its
+// inclusive prefix restarts the running value with it.  Lane L takes 4 consecutive chunks
+// per round of 128.  Called once all aggregates are published; writes INCLUSIVE words.
+static __device__ __noinline__ void resolve_all_prefixes(const ScanParams& p, uint32_t lane) {
+  struct Seg {
+    uint32_t reset;  // the value is a complete prefix
+    Pfx v;
+  };
+  auto seg_op = [](Seg a, Seg b) -> Seg {  // a before b
+    Seg r;
+    r.reset = a.reset | b.reset;
+    r.v = b.reset ? b.v : pfx_op(a.v, b.v);
+    return r;
+  };
+  Seg carry = {1u, {0u, 0ull}};
+  for (uint64_t base = 0; base < p.n_chunks; base += 128) {
+    unsigned long long w[4];
+    Seg g = {0u, {0u, 0ull}};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t idx = base + 4u * lane + (uint32_t)i;
+      w[i] = idx < p.n_chunks ? ld_acquire(&p.status[idx]) : 0ull;
+      if (idx < p.n_chunks) {
+        const Seg e = {(uint32_t)(w[i] >> 62) == kFlagInclusive ? 1u : 0u,
+                       {(uint32_t)((w[i] >> 61) & 1u), w[i] & kCountMask}};
+        g = seg_op(g, e);
+      }
+    }
+    // inclusive scan of the lanes' groups, then the prefix before this lane's group
+    Seg incl = g;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      Seg o;
+      o.reset = __shfl_up_sync(kFull, incl.reset, d);
+      o.v.dead = __shfl_up_sync(kFull, incl.v.dead, d);
+      o.v.count = __shfl_up_sync(kFull, incl.v.count, d);
+      if (lane >= (uint32_t)d) incl = seg_op(o, incl);
+    }
+    Seg before;
+    before.reset = __shfl_up_sync(kFull, incl.reset, 1);
+    before.v.dead = __shfl_up_sync(kFull, incl.v.dead, 1);
+    before.v.count = __shfl_up_sync(kFull, incl.v.count, 1);
+    Pfx x = lane == 0 ? carry.v : seg_op(carry, before).v;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t idx = base + 4u * lane + (uint32_t)i;
+      if (idx < p.n_chunks) {
+        const Pfx v = {(uint32_t)((w[i] >> 61) & 1u), w[i] & kCountMask};
+        const bool inc = (uint32_t)(w[i] >> 62) == kFlagInclusive;
+        x = inc ? v : pfx_op(x, v);
+        if (!inc)
+          st_release(&p.status[idx], pack_status(kFlagInclusive, x.dead, (uint32_t)((w[i] >> 45) & 0xFFFFu), x.count));
+      }
+    }
+    Seg tot;
+    tot.reset = __shfl_sync(kFull, incl.reset, 31);
+    tot.v.dead = __shfl_sync(kFull, incl.v.dead, 31);
+    tot.v.count = __shfl_sync(kFull, incl.v.count, 31);
+    carry = seg_op(carry, tot);
+  }
+}
+
 // Bounded wait on a stage barrier.  Returns false on timeout or when another warp failed.
 __device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity, uint64_t budget,
                                            const DevResult* res) {
@@ -436,6 +499,18 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
   }
   pending |= (1u << issue_first) - 1u;
+  auto cand_class = [&](uint64_t r) -> uint32_t {
+    return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
+  };
+  // the candidate list of every row of the chunk (row k: lane k), looked up by the lanes at
+  // once while the first stages are in flight: the class of the byte that ends the previous
+  // row and the bounds of its list (a chain of dependent global loads, paid once per chunk)
+  uint32_t my_off = 0, my_m = 0;
+  if (active && myrow > 0) {
+    const uint32_t cls = cand_class(myrow);
+    my_off = D.img_off[cls];
+    my_m = D.img_off[cls + 1] - my_off;
+  }
   bool failed = false;
   for (uint32_t b = 0; b < issue_first && !failed; ++b) {
     if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
@@ -449,9 +524,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     const uint32_t b = pos / BOX;
     const uint32_t ch = ((pos % BOX) / 16u) ^ ((k / SWZ_DIV) & SWZ_MASK);
     return *reinterpret_cast<const uint4*>(sm + stage0 + b * SB + k * BOX + ch * 16u);
-  };
-  auto cand_class = [&](uint64_t r) -> uint32_t {
-    return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
   };
 
   uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
@@ -468,6 +540,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       const uint32_t k = k0 + gi;
       const bool valid = k < nrows;
       const uint64_t r = row0 + k;
+      const uint32_t off = __shfl_sync(kFull, my_off, k & 31u), m = __shfl_sync(kFull, my_m, k & 31u);
       uint32_t st = kEmpty, hc = 0;
       bool exact = false;
       if (valid) {
@@ -479,9 +552,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
           exact = true;
         } else {
-          const uint32_t cls = cand_class(r);
-          const uint32_t off = D.img_off[cls];
-          const uint32_t m = D.img_off[cls + 1] - off;
           if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
         }
       }
@@ -556,9 +626,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         }
         continue;
       }
-      const uint32_t cls = cand_class(r);
-      const uint32_t off = D.img_off[cls];
-      const uint32_t m = D.img_off[cls + 1] - off;
+      const uint32_t off = __shfl_sync(kFull, my_off, k), m = __shfl_sync(kFull, my_m, k);
       const bool big = m > 32u * P;
       if (m <= 1 || (big && p.bitmap_words == 0)) {
         if (lane == k) {
@@ -1341,6 +1409,19 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   const Pfx agg = {dmask ? 1u : 0u, csum};
   if (lane == 0 && !skip)
     st_release(&p.status[j], pack_status(kFlagAggregate, agg.dead, E_chunk, agg.count));
+
+  // 7b. the chunk that publishes the last aggregate resolves every chunk's prefix in one pass.
+  //     In a one-wave scan all aggregates appear at about the same time, and the look-back
+  //     alone would carry the inclusive prefixes forward 32 chunks per round trip.
+  if (!skip) {
+    uint32_t last = 0;
+    if (lane == 0) {
+      __threadfence();  // the aggregate above is visible before the count says so
+      last = atomicAdd(&p.result->agg_done, 1u) == (uint32_t)(p.n_chunks - 1) ? 1u : 0u;
+      __threadfence();  // and every other chunk's aggregate before the reads below
+    }
+    if (__shfl_sync(kFull, last, 0)) resolve_all_prefixes(p, lane);
+  }
 
   // 8. decoupled look-back for the exclusive prefix
   Pfx ex = {0, 0};
