@@ -157,8 +157,7 @@ struct DevResult {
   uint32_t conv_max;         // longest merged prefix t over the rows (bytes)
   uint32_t progress;         // bumped by long serial steps; device waits time out only
                              // when it has not moved for their whole budget
-  uint32_t agg_done;         // chunks that published their aggregate (the last one resolves
-                             // every chunk's prefix)
+  uint32_t pad;
   // SM cycles spent by the chunk-owning warps, summed over chunks: speculation (with slot
   // maps), main run, resolution (waits, look-back, row records)
   unsigned long long cyc_spec, cyc_main, cyc_resolve;

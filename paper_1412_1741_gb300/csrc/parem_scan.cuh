@@ -315,69 +315,6 @@ __device__ __forceinline__ unsigned long long pack_status(uint32_t flag, uint32_
          ((unsigned long long)(E & 0xFFFFu) << 45) | (cnt & kCountMask);
 }
 
-// Every chunk's inclusive prefix from the published status words, by one warp: a segmented
-// scan in text order over (dead, count), where a chunk that has already published its
-// inclusive prefix restarts the running value with it.  Lane L takes 4 consecutive chunks
-// per round of 128.  Called once all aggregates are published; writes INCLUSIVE words.
-static __device__ __noinline__ void resolve_all_prefixes(const ScanParams& p, uint32_t lane) {
-  struct Seg {
-    uint32_t reset;  // the value is a complete prefix
-    Pfx v;
-  };
-  auto seg_op = [](Seg a, Seg b) -> Seg {  // a before b
-    Seg r;
-    r.reset = a.reset | b.reset;
-    r.v = b.reset ? b.v : pfx_op(a.v, b.v);
-    return r;
-  };
-  Seg carry = {1u, {0u, 0ull}};
-  for (uint64_t base = 0; base < p.n_chunks; base += 128) {
-    unsigned long long w[4];
-    Seg g = {0u, {0u, 0ull}};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint64_t idx = base + 4u * lane + (uint32_t)i;
-      w[i] = idx < p.n_chunks ? ld_acquire(&p.status[idx]) : 0ull;
-      if (idx < p.n_chunks) {
-        const Seg e = {(uint32_t)(w[i] >> 62) == kFlagInclusive ? 1u : 0u,
-                       {(uint32_t)((w[i] >> 61) & 1u), w[i] & kCountMask}};
-        g = seg_op(g, e);
-      }
-    }
-    // inclusive scan of the lanes' groups, then the prefix before this lane's group
-    Seg incl = g;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      Seg o;
-      o.reset = __shfl_up_sync(kFull, incl.reset, d);
-      o.v.dead = __shfl_up_sync(kFull, incl.v.dead, d);
-      o.v.count = __shfl_up_sync(kFull, incl.v.count, d);
-      if (lane >= (uint32_t)d) incl = seg_op(o, incl);
-    }
-    Seg before;
-    before.reset = __shfl_up_sync(kFull, incl.reset, 1);
-    before.v.dead = __shfl_up_sync(kFull, incl.v.dead, 1);
-    before.v.count = __shfl_up_sync(kFull, incl.v.count, 1);
-    Pfx x = lane == 0 ? carry.v : seg_op(carry, before).v;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const uint64_t idx = base + 4u * lane + (uint32_t)i;
-      if (idx < p.n_chunks) {
-        const Pfx v = {(uint32_t)((w[i] >> 61) & 1u), w[i] & kCountMask};
-        const bool inc = (uint32_t)(w[i] >> 62) == kFlagInclusive;
-        x = inc ? v : pfx_op(x, v);
-        if (!inc)
-          st_release(&p.status[idx], pack_status(kFlagInclusive, x.dead, (uint32_t)((w[i] >> 45) & 0xFFFFu), x.count));
-      }
-    }
-    Seg tot;
-    tot.reset = __shfl_sync(kFull, incl.reset, 31);
-    tot.v.dead = __shfl_sync(kFull, incl.v.dead, 31);
-    tot.v.count = __shfl_sync(kFull, incl.v.count, 31);
-    carry = seg_op(carry, tot);
-  }
-}
-
 // Bounded wait on a stage barrier.  Returns false on timeout or when another warp failed.
 __device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity, uint64_t budget,
                                            const DevResult* res) {
@@ -1410,18 +1347,6 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   if (lane == 0 && !skip)
     st_release(&p.status[j], pack_status(kFlagAggregate, agg.dead, E_chunk, agg.count));
 
-  // 7b. the chunk that publishes the last aggregate resolves every chunk's prefix in one pass.
-  //     In a one-wave scan all aggregates appear at about the same time, and the look-back
-  //     alone would carry the inclusive prefixes forward 32 chunks per round trip.
-  if (!skip) {
-    uint32_t last = 0;
-    if (lane == 0) {
-      __threadfence();  // the aggregate above is visible before the count says so
-      last = atomicAdd(&p.result->agg_done, 1u) == (uint32_t)(p.n_chunks - 1) ? 1u : 0u;
-      __threadfence();  // and every other chunk's aggregate before the reads below
-    }
-    if (__shfl_sync(kFull, last, 0)) resolve_all_prefixes(p, lane);
-  }
 
   // 8. decoupled look-back for the exclusive prefix
   Pfx ex = {0, 0};
