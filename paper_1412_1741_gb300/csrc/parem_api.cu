@@ -179,6 +179,17 @@ int upload_prepared(const Prepared& P, DeviceDfa* out, void** dmem) {
   const size_t o_imgoff = take(P.img_off.size() * 4);
   const size_t o_img = take(P.img.size() * 2);
   const size_t o_rank = take(P.rank.size() * 2);
+  const size_t o_sync = take(256 * 2);
+  // the synchronising bytes: classes whose candidate list has at most one state
+  std::vector<uint16_t> sync(256, (uint16_t)kNoSync16);
+  if (P.n < 0xFFFFu) {
+    for (int b = 0; b < 256; ++b) {
+      const uint32_t c = P.byte_class[b];
+      const uint32_t m = P.img_off[c + 1] - P.img_off[c];
+      if (m == 1) sync[b] = P.img[P.img_off[c]];
+      else if (m == 0 && P.has_dead) sync[b] = (uint16_t)P.dead;
+    }
+  }
   void* mem = nullptr;
   if (cudaMalloc(&mem, off) != cudaSuccess) return PAREM_ERR_OOM;
   uint8_t* base = static_cast<uint8_t*>(mem);
@@ -189,6 +200,7 @@ int upload_prepared(const Prepared& P, DeviceDfa* out, void** dmem) {
   e = e == cudaSuccess ? cudaMemcpy(base + o_imgoff, P.img_off.data(), P.img_off.size() * 4, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cudaMemcpy(base + o_img, P.img.data(), P.img.size() * 2, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cudaMemcpy(base + o_rank, P.rank.data(), P.rank.size() * 2, cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cudaMemcpy(base + o_sync, sync.data(), 256 * 2, cudaMemcpyHostToDevice) : e;
   if (e != cudaSuccess) {
     cudaFree(mem);
     return PAREM_ERR_CUDA;
@@ -222,6 +234,7 @@ int upload_prepared(const Prepared& P, DeviceDfa* out, void** dmem) {
   D.win = P.win;
   D.pair_hot = P.pair_hot;
   D.pair_off = P.pair_off;
+  D.sync_state = reinterpret_cast<const uint16_t*>(base + o_sync);
   *out = D;
   *dmem = mem;
   return PAREM_OK;

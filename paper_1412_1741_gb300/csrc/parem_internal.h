@@ -54,9 +54,12 @@ constexpr uint32_t kPairMaxWarps = 24;  // warps per block of its pass 1 (regist
 // tables leave less shared memory for stages, 64 bytes (64-byte swizzle) otherwise.
 constexpr uint32_t box_bytes(uint32_t layout) { return layout == kClassPair ? 32u : kBox; }
 constexpr uint32_t kNoSync = 0xFFFFFFFFu;  // Prepared::sync_len: the candidate sets did not synchronise
-// Shared memory of every kernel starts with the column map (512 B reserved) followed by the
-// table at this fixed offset, so table reads use an immediate offset.
-constexpr uint32_t kTableOff = 512;
+// Shared memory of every kernel starts with the column map (512 B reserved), then the
+// synchronising-byte table (256 u16 at kSyncOff), then the table at this fixed offset, so
+// table reads use an immediate offset.
+constexpr uint32_t kSyncOff = 512;
+constexpr uint32_t kTableOff = 1024;
+constexpr uint32_t kNoSync16 = 0xFFFFu;  // sync_state entry of a byte that does not synchronise
 
 // Chunk status word (64 bit), published with release semantics:
 //   [63:62] flag  0 none, 1 MAPPED (end state E known), 2 AGGREGATE (E, dead, count),
@@ -121,6 +124,10 @@ struct DeviceDfa {
   uint32_t stride_k4, stride_wts, stride_krep, stride_kmrep;
   uint32_t win;                   // kClassWin (see Prepared)
   uint32_t pair_hot, pair_off;    // kClassPair (see Prepared)
+  // 256 entries: for a byte whose class leads every live state to one state (its candidate
+  // list img(c) has one state), that state; the dead state when the list is empty; kNoSync16
+  // otherwise (or for every byte when a state id could be 0xFFFF)
+  const uint16_t* sync_state;
 };
 
 // Per-segment record for the emit pass: the matches of the row lie in the row-relative

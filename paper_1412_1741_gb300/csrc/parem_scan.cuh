@@ -190,13 +190,24 @@ struct Tab {
   }
 };
 
-// Stage the column map and (shared layouts) the table into shared memory.
+// The synchronising-byte table into shared memory at kSyncOff (all kNoSync16 when the DFA
+// has none).
+__device__ __forceinline__ void load_sync(uint8_t* sm, const DeviceDfa& D) {
+  uint4* dst = reinterpret_cast<uint4*>(sm + kSyncOff);
+  const uint4* src = reinterpret_cast<const uint4*>(D.sync_state);
+  for (uint32_t i = threadIdx.x; i < 512 / 16; i += blockDim.x)
+    dst[i] = src != nullptr ? src[i] : make_uint4(kFull, kFull, kFull, kFull);
+}
+
+// Stage the column map, the synchronising-byte table and (shared layouts) the table into
+// shared memory.
 template <int LAYOUT, int ESIZE>
 __device__ __forceinline__ void load_tables(uint8_t* sm, const DeviceDfa& D) {
   const uint32_t cm_bytes = Tab<LAYOUT, ESIZE>::kWide ? 512u : 256u;
   const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
   uint4* dst = reinterpret_cast<uint4*>(sm);
   for (uint32_t i = threadIdx.x; i < cm_bytes / 16; i += blockDim.x) dst[i] = src[i];
+  load_sync(sm, D);
   if (!Tab<LAYOUT, ESIZE>::kGlobal) {
     const uint4* ts = reinterpret_cast<const uint4*>(D.table);
     uint4* td = reinterpret_cast<uint4*>(sm + kTableOff);
@@ -209,6 +220,7 @@ __device__ __forceinline__ void load_tables_dyn(uint8_t* sm, const DeviceDfa& D,
   const uint4* src = reinterpret_cast<const uint4*>(D.colmap);
   uint4* dst = reinterpret_cast<uint4*>(sm);
   for (uint32_t i = threadIdx.x; i < 512 / 16; i += blockDim.x) dst[i] = src[i];
+  load_sync(sm, D);
   if (smem_tier) {
     const uint4* ts = reinterpret_cast<const uint4*>(D.table);
     uint4* td = reinterpret_cast<uint4*>(sm + kTableOff);
@@ -464,6 +476,39 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
   };
 
   uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
+  // Rows that reach a synchronising byte early need no speculation: a byte whose class has
+  // a one-state candidate list (Algorithm 1's R = S n L of the position after it is that
+  // state for every live start) fixes the run.  Each lane looks for one in the staged bytes of
+  // its row and runs that state to the next 16-byte boundary; the row is then merged at that
+  // offset (the resolved start replays the bytes before it, as for any merged prefix).
+  uint32_t my_sync = 0;
+  if (active && myrow > 0 && !p.enum_all && !failed && staged >= 32) {
+    const uint16_t* sync = reinterpret_cast<const uint16_t*>(sm + kSyncOff);
+    uint32_t t0 = kEmpty, x = 0;
+    for (uint32_t pos = 0; pos + 16 < staged && t0 == kEmpty; pos += 16) {
+      const uint4 v = staged16(lane, pos);
+#pragma unroll
+      for (uint32_t q = 0; q < 16; ++q) {
+        if (t0 == kEmpty) {
+          const uint32_t z = sync[byte_of(v, (int)q)];
+          if (z != kNoSync16) {
+            t0 = pos + q;
+            x = z;
+          }
+        }
+      }
+    }
+    if (t0 != kEmpty) {
+      const uint32_t t1 = (t0 + 16u) & ~15u;
+      const uint4 v = staged16(lane, t0 & ~15u);
+#pragma unroll
+      for (uint32_t q = 0; q < 16; ++q)
+        if (q > (t0 & 15u)) x = tab.next(x, tab.col(byte_of(v, (int)q)));
+      my_t = t1;
+      my_sigma = x;
+      my_sync = 1;
+    }
+  }
   // speculation work of this chunk (warp-uniform): live candidates after each merge check
   // times the steps to the next check
   unsigned long long spec_lk = 0;
@@ -478,6 +523,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       const bool valid = k < nrows;
       const uint64_t r = row0 + k;
       const uint32_t off = __shfl_sync(kFull, my_off, k & 31u), m = __shfl_sync(kFull, my_m, k & 31u);
+      const bool synced = __shfl_sync(kFull, my_sync, k & 31u) != 0;
       uint32_t st = kEmpty, hc = 0;
       bool exact = false;
       if (valid) {
@@ -488,13 +534,13 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
             if (st == dead) st = kEmpty;
           }
           exact = true;
-        } else {
+        } else if (!synced) {
           if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
         }
       }
       // a row whose group has at most one live lane is already merged at t = 0
       unsigned live = __ballot_sync(kFull, st != kEmpty);
-      bool done = exact || !valid || __popc(live & gmask) <= 1;
+      bool done = exact || !valid || synced || __popc(live & gmask) <= 1;
       uint32_t pos = 0, outcome = 1;
       const uint8_t* grow = body + (row0 + (valid ? k : 0u)) * p.S;
       const uint32_t kk = valid ? k : 0u;
@@ -541,7 +587,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       const uint32_t o_out = __shfl_sync(kFull, outcome, from);
       const uint32_t o_pos = __shfl_sync(kFull, pos, from);
       const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
-      if (lane >= k0 && lane < k0 + rpp && lane < nrows) {
+      if (lane >= k0 && lane < k0 + rpp && lane < nrows && !my_sync) {
         my_conv = o_out == 1;
         my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
         my_sigma = o_out == 1 ? o_sig : kEmpty;
@@ -563,6 +609,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         }
         continue;
       }
+      if (__shfl_sync(kFull, my_sync, k)) continue;  // merged at a synchronising byte
       const uint32_t off = __shfl_sync(kFull, my_off, k), m = __shfl_sync(kFull, my_m, k);
       const bool big = m > 32u * P;
       if (m <= 1 || (big && p.bitmap_words == 0)) {
