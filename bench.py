@@ -730,6 +730,86 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_enum_compare(args, rank, world, local_rank):
+    """PaREM against the general enumeration approach (every live state a candidate of every
+    chunk) on the paper's own automaton (Table I, 'parallel', 9 states) over uniform texts of
+    2^26 .. 2^30 symbols, the lengths of the paper's experiments (Section IV, Fig. 6).  Both
+    arms run the same kernels; one JSON line per length with both arms' times, speculation
+    lookups per byte, the candidate-run counts of the worked example's argument (Section II-C)
+    and parity of both arms with the oracle.  Rank 0 only."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    import paper_1412_1741_gb300 as pm
+    from oracle import oracle
+    from paper_1412_1741_gb300 import workloads as wl
+
+    if rank != 0:
+        return
+    ge.build()
+    oracle.build()
+    dev, _ = setup_rank(local_rank, 1)
+    spec = wl.parallel_dfa()
+    info = pm.parem_prepare_info(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+    peak, peak_kind = measured_peaks()
+    for k in range(args.enum_min_log2, args.enum_max_log2 + 1):
+        n = 1 << k
+        text = wl.uniform_text_device(n, 5, dev, seed=11)
+        host = text.cpu().numpy()
+        want = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, host)
+        arms = {}
+        for name, enum in (("parem", 0), ("enumeration", 1)):
+            dfa = pm.parem_load_dfa(spec.table, spec.byte_to_symbol, spec.start, spec.accept)
+            pos = torch.full((max(1, want.match_count),), -1, dtype=torch.int64, device=dev)
+            opts = pm.MatchOpts(enumerate_all=enum)
+            timed = pm.MatchOpts(enumerate_all=enum, record_kernel_times=1)
+            for _ in range(args.warmup):
+                pm.parem_match_ex(dfa, text, pos, opts)
+            torch.cuda.synchronize()
+            stream = torch.cuda.current_stream()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                r = pm.parem_match_ex(dfa, text, pos, opts)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / args.steps
+            scan = []
+            for _ in range(5):
+                pm.parem_match_ex(dfa, text, pos, timed)
+                scan.append(pm.parem_last_stats()["scan_ms"])
+            st = pm.parem_last_stats()
+            ok = (r.final_state, r.accepted, r.match_count) == (want.final_state, want.accepted, want.match_count) and \
+                np.array_equal(pos[:want.match_count].cpu().numpy().view(np.uint64), want.positions)
+            arms[name] = {"ms_per_step": round(ms, 4), "gbs": round(n / (ms / 1e3) / 1e9, 2),
+                          "scan_ms": round(float(np.median(scan)), 4),
+                          "spec_lookups_per_byte": round(st["spec_lookups"] / n, 6),
+                          "rows": st["rows"], "chunks": st["chunks"], "segment_bytes": st["segment_bytes"],
+                          "parity": bool(ok)}
+            dfa.free()
+        line = {
+            "metric": "PaREM vs general enumeration: time ratio (enumeration / PaREM) on 1 GB300",
+            "value": round(arms["enumeration"]["ms_per_step"] / arms["parem"]["ms_per_step"], 3), "unit": "x",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "Table I automaton ('parallel', 9 states, 5 symbols), uniform i.i.d. text over "
+                                   "{p,a,r,e,l} (the paper's experiment lengths)", "text_bytes": n, "log2_n": k,
+                       "matches": want.match_count},
+            "parem": arms["parem"], "enumeration": arms["enumeration"],
+            "candidate_runs_per_chunk": {"parem_mean": round(info.mean_candidates, 3), "parem_max": info.max_candidates,
+                                         "enumeration": info.compact_states - int(info.has_dead),
+                                         "note": "candidates per row start: |img(class)| for PaREM (Algorithm 1's "
+                                                 "R = S n L), every live state for enumeration"},
+            "parity": arms["parem"]["parity"] and arms["enumeration"]["parity"],
+            "paper_context": "the paper reports 2.3x at 48 threads on 1.07e9 symbols and 1.04x at 6 threads on 6.69e7 "
+                             "(Section IV-A); other hardware, context only",
+            "peak_gbs": peak,
+        }
+        print(json.dumps(line), flush=True)
+        del text, host
+
+
 # ---------------------------------------------------------------------------------------
 # ncu summaries for profiles/ (read back from reports; no GPU needed)
 # ---------------------------------------------------------------------------------------
@@ -855,6 +935,10 @@ def main():
                     help="candidate set = every live state (the General Enumeration baseline)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default line without its batched and serving parts")
+    ap.add_argument("--enum-compare", action="store_true",
+                    help="PaREM against general enumeration on the Table I automaton, one line per length")
+    ap.add_argument("--enum-min-log2", type=int, default=26)
+    ap.add_argument("--enum-max-log2", type=int, default=30)
     ap.add_argument("--ncu-report", default="", help="summarise this --set full report into profiles/")
     ap.add_argument("--ncu-launches", default="", help="summarise this ncu --csv launch list into profiles/")
     ap.add_argument("--ncu-command", default="", help="the command that made the report (recorded)")
@@ -876,6 +960,9 @@ def main():
         CONFIGS[args.config]["workload"] += f" (resized to {args.size_mb} MiB)"
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.enum_compare:
+        run_enum_compare(args, rank, world, local_rank)
         return
     if args.config == "d4":
         run_batch(args, rank, world, local_rank)
