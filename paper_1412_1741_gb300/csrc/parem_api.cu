@@ -591,7 +591,12 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   const uint64_t o_rows = round_up(o_segrec + (emit ? pl.R * sizeof(SegRec) : 0), 256);
   const uint64_t o_slot = round_up(o_rows + (emit ? pl.R * kRowSlotBytes : 0), 256);
   const uint64_t slot_bytes = pl.serial ? 0 : pl.R * (uint64_t)pl.cand_stride * 4;
-  const uint64_t total = round_up(std::max<uint64_t>(o_slot + 2 * slot_bytes, 256), 256);
+  // dense matches: pass 1 records them as one bit per body byte and the emit pass expands
+  // the bits (the pair and stride layouts count in their own ways and keep the replay)
+  const bool bits = emit && pl.dense && pl.R && P.layout != kByteStride && P.layout != kClassPair;
+  const uint64_t o_bits = round_up(o_slot + 2 * slot_bytes, 256);
+  const uint64_t bits_bytes = bits ? round_up((pl.R * pl.S + pl.tail + 7) / 8 + 16, 256) : 0;
+  const uint64_t total = round_up(std::max<uint64_t>(o_bits + bits_bytes, 256), 256);
   rc = ensure(&sc->dev, &sc->bytes, total);
   if (rc != PAREM_OK) return rc;
   uint8_t* sb = static_cast<uint8_t*>(sc->dev);
@@ -630,7 +635,9 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   p.slots = emit ? reinterpret_cast<uint32_t*>(sb + o_rows) : nullptr;
   p.slot_end = reinterpret_cast<uint32_t*>(sb + o_slot);
   p.slot_cnt = reinterpret_cast<uint32_t*>(sb + o_slot + slot_bytes);
-  p.stream_emit = (emit && pl.dense && pl.R) ? 1u : 0u;
+  p.stream_emit = (emit && pl.dense && pl.R && !bits) ? 1u : 0u;
+  p.match_bits = bits ? reinterpret_cast<uint32_t*>(sb + o_bits) : nullptr;
+  if (bits) p.sparse_count = 0;
   p.positions = emit ? positions : nullptr;
   p.capacity = emit ? capacity : 0;
 

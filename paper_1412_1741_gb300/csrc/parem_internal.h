@@ -22,6 +22,8 @@ constexpr uint32_t kSpecBytes = kLanes * kLaneCand * 2 + kLanes * 4 + 48;
 constexpr uint32_t kHeadFlag = 1u;       // SegRec.flags: row 0 re-runs the unaligned head
 constexpr uint32_t kSlotsFlag = 2u;      // SegRec.flags: every main-run match of the row is in its slots
 constexpr uint32_t kPreFlag = 4u;        // SegRec.flags: replay the merged prefix [0, t) from x
+constexpr uint32_t kBitsFlag = 8u;       // SegRec.flags: the main-run matches of [t, row end) are in
+                                         // the match bitmap
 constexpr uint32_t kRowSlots = 16;       // match positions pass 1 records per row
 constexpr uint64_t kMaxText = 1ull << 45;
 
@@ -209,6 +211,9 @@ struct ScanParams {
                            // count (by a replay of the vector) only where it is accepting
   uint32_t stream_emit;    // dense matches: the emit pass streams the rows through shared
                            // memory by TMA as pass 1 does (k_emit_stream)
+  uint32_t* match_bits;    // dense matches: one bit per body byte (bit i: body byte i ends a
+                           // match), written by pass 1's main run and read by k_emit_bits;
+                           // nullptr = off
   uint64_t wait_budget;    // clock64 cycles
   int64_t skip_publish;    // test hook (-1 off)
   // scratch

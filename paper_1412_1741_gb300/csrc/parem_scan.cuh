@@ -1068,6 +1068,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
     if (run) {
       const uint32_t col0 = blk * BOX;
+      unsigned long long bmask = 0;  // match bits of this block (match bitmap only)
 #pragma unroll
       for (uint32_t i = 0; i < BOX / 16; ++i) {
         const uint32_t col = col0 + i * 16u;
@@ -1158,6 +1159,17 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
                 mu += (x >= A);
               }
             }
+          } else if (p.match_bits != nullptr) {
+            // dense matches: the accepting steps of the vector as a 16-bit mask for the match
+            // bitmap (stored once per block below)
+            uint32_t mb = 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              s = tab.next(s, tab.col(byte_of(v[i], q)));
+              mb |= (s >= A ? 1u : 0u) << q;
+            }
+            mu += __popc(mb);
+            bmask |= (unsigned long long)mb << (16u * i);
           } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -1188,6 +1200,15 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
         }
       }
+      if (p.match_bits != nullptr) {
+        // bits [myrow * S + col0, + BOX) of the body: BOX-bit aligned (S and col0 are)
+        const uint64_t bit0 = myrow * p.S + col0;
+        if constexpr (BOX == 64) {
+          reinterpret_cast<unsigned long long*>(p.match_bits)[bit0 / 64] = bmask;
+        } else {
+          p.match_bits[bit0 / 32] = (uint32_t)bmask;
+        }
+      }
     }
   }
   if (failed) return;
@@ -1211,6 +1232,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         cur = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       }
       const uint32_t n_here = min(16u, tl - o);
+      uint32_t tbits = 0;
 #pragma unroll
       for (uint32_t q = 0; q < 16; ++q) {
         if (q < n_here) {
@@ -1218,6 +1240,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           s = tab.next(s, tab.col(byte_of(cur, (int)q)));
           if (s >= A) {
             ++mu;
+            tbits |= 1u << q;
             const uint32_t at = (uint32_t)p.S + o + q;
             if (fv == kEmpty) {
               fv = at;
@@ -1231,6 +1254,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           }
         }
       }
+      // bits [R * S + o, + 16) of the body (16-bit aligned)
+      if (p.match_bits != nullptr)
+        reinterpret_cast<uint16_t*>(p.match_bits)[(p.R * p.S + o) / 16] = (uint16_t)tbits;
     }
   }
   const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
@@ -1494,6 +1520,11 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         sr.ls = ls;
         // every main-run match was recorded by pass 1: the emit pass only copies them
         if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
+        // or they are in the match bitmap from the main run's start my_t on
+        if (main_live && p.match_bits != nullptr) {
+          sr.flags |= kBitsFlag;
+          sr.t = my_t;
+        }
       }
       p.segrec[myrow] = sr;
     }
@@ -1928,6 +1959,86 @@ __global__ void __launch_bounds__(1024, 1)
   publish_result(p, p.ticket + kDoneEmitWord);
 }
 
+// Dense emission from the match bitmap of pass 1: one warp per row with matches.  Lane 0
+// replays the head bytes or the merged prefix [0, t) from the row's start (as k_emit does);
+// then, 512 bytes of the row at a time, every lane takes 16 bits of the bitmap, the lanes'
+// positions go to a per-warp buffer in shared memory at their scan offsets, and the warp
+// writes the buffer in order with consecutive addresses.  Rows without bits (speculation
+// that never merged) are replayed by lane 0.
+constexpr uint32_t kEmitBitsWarps = 16;    // warps per block of k_emit_bits
+constexpr uint32_t kEmitBitsBuf = 512;     // positions a warp buffers per round (32 x 16 bits)
+
+template <int LAYOUT, int ESIZE>
+__global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanParams p) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  uint8_t* const sm = smem_raw;
+  const DeviceDfa& D = p.dfa;
+  load_tables<LAYOUT, ESIZE>(sm, D);
+  __syncthreads();
+  Tab<LAYOUT, ESIZE> tab;
+  tab.sm = sm;
+  tab.gtable = D.table;
+  tab.rowbytes = D.rowbytes;
+  tab.smem_tier = 1;
+  tab.set_win(D.win);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t tbytes = Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes;
+  uint32_t* const buf = reinterpret_cast<uint32_t*>(sm + ((kTableOff + tbytes + 15u) & ~15u)) + warp * kEmitBitsBuf;
+  const uint16_t* bits16 = reinterpret_cast<const uint16_t*>(p.match_bits);
+  const uint64_t step = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < p.R; r += step) {
+    const SegRec sr = p.segrec[r];
+    if (sr.count == 0 || sr.offset >= p.capacity) continue;
+    if (!(sr.flags & kBitsFlag)) {
+      if (lane == 0) emit_row<LAYOUT, ESIZE>(tab, p, r);
+      continue;
+    }
+    const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
+    uint64_t o = sr.offset;
+    if (lane == 0) {
+      uint32_t x = sr.x;
+      if (sr.flags & kHeadFlag) {
+        for (uint64_t i = 0; i < p.h && o < end; ++i) {
+          x = tab.next(x, tab.col(ldg8(p.text + i)));
+          if (x >= p.dfa.first_accept) p.positions[o++] = p.pos_base + i;
+        }
+      } else if (sr.flags & kPreFlag) {
+        emit_range(tab, p, r, 0u, sr.t, x, o, end);
+      }
+    }
+    o = __shfl_sync(kFull, o, 0);
+    const uint32_t rowlen = (uint32_t)(p.S + (r == p.R - 1 ? p.tail : 0));
+    const uint64_t rbit = r * p.S;                     // body bit of the row's first byte
+    const uint64_t gpos = p.pos_base + p.h + r * p.S;  // text position of the row's first byte
+    for (uint32_t base = sr.t; base < rowlen && o < end; base += kEmitBitsBuf) {
+      const uint32_t at = base + 16u * lane;  // sr.t is a multiple of 16
+      uint32_t m = 0;
+      if (at < rowlen) {
+        m = bits16[(rbit + at) / 16];
+        if (at + 16u > rowlen) m &= (1u << (rowlen - at)) - 1u;
+      }
+      const uint32_t c = __popc(m);
+      uint32_t incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+      }
+      const uint32_t total = __shfl_sync(kFull, incl, 31);
+      uint32_t k = incl - c;
+      while (m != 0u) {
+        buf[k++] = at + (uint32_t)(__ffs(m) - 1);
+        m &= m - 1u;
+      }
+      __syncwarp();
+      for (uint32_t i = lane; i < total && o + i < end; i += 32) p.positions[o + i] = gpos + buf[i];
+      __syncwarp();
+      o += total;
+    }
+  }
+  publish_result(p, p.ticket + kDoneEmitWord);
+}
+
 // ---------------------------------------------------------------------------------------
 // Texts too short for one row: a single thread runs the plain loop on the device.
 // ---------------------------------------------------------------------------------------
@@ -2128,9 +2239,20 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, int block, size_t smem,
                         cudaStream_t stream) {
-  static std::atomic<size_t> limits[64], limits_stream[64];
+  static std::atomic<size_t> limits[64], limits_stream[64], limits_bits[64];
   // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
   static std::atomic<uint64_t> choice[64];
+  if (p.match_bits != nullptr) {
+    // dense matches recorded as bits by pass 1: two blocks of 16 warps per SM
+    auto kern = k_emit_bits<LAYOUT, ESIZE>;
+    const size_t sm_bytes = ((smem + 15) & ~(size_t)15) + (size_t)kEmitBitsWarps * kEmitBitsBuf * 4;
+    cudaError_t e = raise_smem_limit(kern, sm_bytes, limits_bits);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (p.R + kEmitBitsWarps - 1) / kEmitBitsWarps;
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid * 2, want));
+    kern<<<blocks, kEmitBitsWarps * 32, sm_bytes, stream>>>(p);
+    return cudaGetLastError();
+  }
   if (p.stream_emit && tm != nullptr) {
     // dense matches: pass 1's launch shape (one block per SM, warps as shared memory allows)
     auto kern = k_emit_stream<LAYOUT, ESIZE>;
