@@ -229,10 +229,13 @@ __device__ __forceinline__ void load_tables_dyn(uint8_t* sm, const DeviceDfa& D,
 }
 
 // Run [0, len) of a 16-byte aligned global range from state x.  Adds the matches to *cnt
-// and returns the end state; stops early (returning dead) once the run is dead.
+// and returns the end state; stops early (returning dead) once the run is dead.  With bits,
+// also writes each vector's 16 match bits (bits[o / 16] for the vector at o) to the match
+// bitmap of the range.
 template <int LAYOUT, int ESIZE>
 __device__ uint32_t run_range16(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p, uint64_t len,
-                                uint32_t x, uint32_t dead, uint32_t first_accept, uint32_t* cnt) {
+                                uint32_t x, uint32_t dead, uint32_t first_accept, uint32_t* cnt,
+                                uint16_t* bits = nullptr) {
   uint32_t c = 0;
   const uint4 zero = make_uint4(0, 0, 0, 0);
   // two vectors in flight ahead of the one being consumed
@@ -241,10 +244,21 @@ __device__ uint32_t run_range16(const Tab<LAYOUT, ESIZE>& tab, const uint8_t* p,
     const uint4 v = a;
     a = b;
     b = o + 48 <= len ? ldg16(p + o + 32) : zero;
+    if (bits != nullptr) {
+      uint32_t m = 0;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      x = tab.next(x, tab.col(byte_of(v, i)));
-      c += (x >= first_accept);
+      for (int i = 0; i < 16; ++i) {
+        x = tab.next(x, tab.col(byte_of(v, i)));
+        m |= (x >= first_accept ? 1u : 0u) << i;
+      }
+      c += __popc(m);
+      bits[o / 16] = (uint16_t)m;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        x = tab.next(x, tab.col(byte_of(v, i)));
+        c += (x >= first_accept);
+      }
     }
     if (x == dead) break;
   }
@@ -1264,6 +1278,10 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
 #if PAREM_PHASE_STATS
   const uint32_t clk2 = (uint32_t)clock64();
 #endif
+  // the match bitmap of row r (the merged prefix replays below write its bits [0, t))
+  auto row_bits = [&](uint64_t r) -> uint16_t* {
+    return p.match_bits != nullptr ? reinterpret_cast<uint16_t*>(p.match_bits) + (r * p.S) / 16 : nullptr;
+  };
   // 5. the chunk's end state is known now if every row merged
   //    (or if at least its last row did: E_last does not depend on the chunk's start, and
   //    publishing it now keeps chunks with unmerged rows from forming a chain)
@@ -1281,7 +1299,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       dies_k = 1;
       died_pre = 1;
     } else {
-      const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre_k);
+      const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, x_k, dead, A, &pre_k, row_bits(myrow));
       if (y == dead) {
         dies_k = 1;
         died_pre = 1;
@@ -1333,7 +1351,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         died_pre = 1;
         cnt_k = 0;
       } else {
-        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre_k);
+        const uint32_t y = run_range16(tab, body + myrow * p.S, my_t, s_j, dead, A, &pre_k, row_bits(myrow));
         if (y == dead) {
           dies_k = 1;
           died_pre = 1;
@@ -1370,7 +1388,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
           cnt = hk + muk;
           x = Ek;
         } else if (ck) {
-          const uint32_t y = run_range16(tab, body + r * p.S, tk, x, dead, A, &pre);
+          const uint32_t y = run_range16(tab, body + r * p.S, tk, x, dead, A, &pre, row_bits(r));
           if (y == dead) {
             cnt = pre;
             dpre = 1;
@@ -1520,11 +1538,10 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         sr.ls = ls;
         // every main-run match was recorded by pass 1: the emit pass only copies them
         if (main_live && p.slots != nullptr && nrec == mu && mu <= kRowSlots) sr.flags |= kSlotsFlag;
-        // or they are in the match bitmap from the main run's start my_t on
-        if (main_live && p.match_bits != nullptr) {
-          sr.flags |= kBitsFlag;
-          sr.t = my_t;
-        }
+        // or every match of the row is in the match bitmap: the prefix [0, t) replayed from the
+        // row's true start wrote its bits, the main run the rest (a run that died inside the
+        // prefix is replayed by the emit pass instead)
+        if (!died_pre && p.match_bits != nullptr) sr.flags |= kBitsFlag;
       }
       p.segrec[myrow] = sr;
     }
@@ -1995,28 +2012,29 @@ __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanPar
     }
     const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
     uint64_t o = sr.offset;
-    if (lane == 0) {
+    if (lane == 0 && (sr.flags & kHeadFlag)) {  // row 0's bytes before the aligned body
       uint32_t x = sr.x;
-      if (sr.flags & kHeadFlag) {
-        for (uint64_t i = 0; i < p.h && o < end; ++i) {
-          x = tab.next(x, tab.col(ldg8(p.text + i)));
-          if (x >= p.dfa.first_accept) p.positions[o++] = p.pos_base + i;
-        }
-      } else if (sr.flags & kPreFlag) {
-        emit_range(tab, p, r, 0u, sr.t, x, o, end);
+      for (uint64_t i = 0; i < p.h && o < end; ++i) {
+        x = tab.next(x, tab.col(ldg8(p.text + i)));
+        if (x >= p.dfa.first_accept) p.positions[o++] = p.pos_base + i;
       }
     }
     o = __shfl_sync(kFull, o, 0);
     const uint32_t rowlen = (uint32_t)(p.S + (r == p.R - 1 ? p.tail : 0));
     const uint64_t rbit = r * p.S;                     // body bit of the row's first byte
     const uint64_t gpos = p.pos_base + p.h + r * p.S;  // text position of the row's first byte
-    for (uint32_t base = sr.t; base < rowlen && o < end; base += kEmitBitsBuf) {
-      const uint32_t at = base + 16u * lane;  // sr.t is a multiple of 16
-      uint32_t m = 0;
-      if (at < rowlen) {
-        m = bits16[(rbit + at) / 16];
-        if (at + 16u > rowlen) m &= (1u << (rowlen - at)) - 1u;
-      }
+    // the next round's bits are loaded while this round's positions are written
+    auto load_bits = [&](uint32_t at) -> uint32_t {
+      if (at >= rowlen) return 0u;
+      uint32_t m = bits16[(rbit + at) / 16];
+      if (at + 16u > rowlen) m &= (1u << (rowlen - at)) - 1u;
+      return m;
+    };
+    uint32_t m_next = load_bits(16u * lane);
+    for (uint32_t base = 0; base < rowlen && o < end; base += kEmitBitsBuf) {
+      const uint32_t at = base + 16u * lane;
+      uint32_t m = m_next;
+      m_next = load_bits(at + kEmitBitsBuf);
       const uint32_t c = __popc(m);
       uint32_t incl = c;
 #pragma unroll
