@@ -1364,7 +1364,9 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
   } else {
-    // slow path: walk the rows in order from s_j (lane 0 works, the lanes keep results)
+    // slow path: walk the rows in order from s_j (lane 0 works, the lanes keep results); the
+    // match bitmap words the lanes' main runs wrote are ordered before lane 0's prefix bits
+    __syncwarp();
     uint32_t x = s_j;
     for (uint32_t k = 0; k < nrows; ++k) {
       const uint32_t tk = __shfl_sync(kFull, my_t, k);
@@ -1977,13 +1979,15 @@ __global__ void __launch_bounds__(1024, 1)
 }
 
 // Dense emission from the match bitmap of pass 1: one warp per row with matches.  Lane 0
-// replays the head bytes or the merged prefix [0, t) from the row's start (as k_emit does);
-// then, 512 bytes of the row at a time, every lane takes 16 bits of the bitmap, the lanes'
-// positions go to a per-warp buffer in shared memory at their scan offsets, and the warp
-// writes the buffer in order with consecutive addresses.  Rows without bits (speculation
-// that never merged) are replayed by lane 0.
+// replays row 0's head bytes (before the aligned body, outside the bitmap); then, 1,024
+// bytes of the row at a time, every lane takes 32 bits of the bitmap, writes its positions
+// (relative to the round, 16 bits each) into a per-warp buffer in shared memory at its scan
+// offset -- two bits per step, the lowest from the front and the highest from the back --
+// and the warp writes the buffer in order with consecutive addresses.  Rows without bits
+// (a run that died inside its merged prefix, or speculation that never merged) are
+// replayed by lane 0.
 constexpr uint32_t kEmitBitsWarps = 16;    // warps per block of k_emit_bits
-constexpr uint32_t kEmitBitsBuf = 512;     // positions a warp buffers per round (32 x 16 bits)
+constexpr uint32_t kEmitBitsRound = 1024;  // row bytes per round (32 lanes x 32 bits)
 
 template <int LAYOUT, int ESIZE>
 __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanParams p) {
@@ -2000,8 +2004,8 @@ __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanPar
   tab.set_win(D.win);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t tbytes = Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes;
-  uint32_t* const buf = reinterpret_cast<uint32_t*>(sm + ((kTableOff + tbytes + 15u) & ~15u)) + warp * kEmitBitsBuf;
-  const uint16_t* bits16 = reinterpret_cast<const uint16_t*>(p.match_bits);
+  uint16_t* const buf = reinterpret_cast<uint16_t*>(sm + ((kTableOff + tbytes + 15u) & ~15u)) + warp * kEmitBitsRound;
+  const uint32_t* bits32 = p.match_bits;
   const uint64_t step = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < p.R; r += step) {
     const SegRec sr = p.segrec[r];
@@ -2021,20 +2025,19 @@ __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanPar
     }
     o = __shfl_sync(kFull, o, 0);
     const uint32_t rowlen = (uint32_t)(p.S + (r == p.R - 1 ? p.tail : 0));
-    const uint64_t rbit = r * p.S;                     // body bit of the row's first byte
-    const uint64_t gpos = p.pos_base + p.h + r * p.S;  // text position of the row's first byte
+    const uint64_t rword = (r * p.S) / 32;              // bitmap word of the row's first byte
+    const uint64_t gpos = p.pos_base + p.h + r * p.S;   // text position of the row's first byte
     // the next round's bits are loaded while this round's positions are written
     auto load_bits = [&](uint32_t at) -> uint32_t {
       if (at >= rowlen) return 0u;
-      uint32_t m = bits16[(rbit + at) / 16];
-      if (at + 16u > rowlen) m &= (1u << (rowlen - at)) - 1u;
+      uint32_t m = bits32[rword + at / 32];
+      if (rowlen - at < 32u) m &= (1u << (rowlen - at)) - 1u;
       return m;
     };
-    uint32_t m_next = load_bits(16u * lane);
-    for (uint32_t base = 0; base < rowlen && o < end; base += kEmitBitsBuf) {
-      const uint32_t at = base + 16u * lane;
+    uint32_t m_next = load_bits(32u * lane);
+    for (uint32_t base = 0; base < rowlen && o < end; base += kEmitBitsRound) {
       uint32_t m = m_next;
-      m_next = load_bits(at + kEmitBitsBuf);
+      m_next = load_bits(base + kEmitBitsRound + 32u * lane);
       const uint32_t c = __popc(m);
       uint32_t incl = c;
 #pragma unroll
@@ -2043,13 +2046,21 @@ __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanPar
         if (lane >= (uint32_t)d) incl += y;
       }
       const uint32_t total = __shfl_sync(kFull, incl, 31);
-      uint32_t k = incl - c;
+      uint32_t lo = incl - c, hi = incl;
+      const uint32_t rel = 32u * lane;
       while (m != 0u) {
-        buf[k++] = at + (uint32_t)(__ffs(m) - 1);
+        buf[lo++] = (uint16_t)(rel + (uint32_t)(__ffs(m) - 1));
         m &= m - 1u;
+        if (m != 0u) {
+          const uint32_t qh = 31u - (uint32_t)__clz(m);
+          buf[--hi] = (uint16_t)(rel + qh);
+          m ^= 1u << qh;
+        }
       }
       __syncwarp();
-      for (uint32_t i = lane; i < total && o + i < end; i += 32) p.positions[o + i] = gpos + buf[i];
+      const uint64_t rb = gpos + base;
+      const uint32_t lim = (uint32_t)(end - o < total ? end - o : total);
+      for (uint32_t i = lane; i < lim; i += 32) p.positions[o + i] = rb + buf[i];
       __syncwarp();
       o += total;
     }
@@ -2263,7 +2274,7 @@ cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, in
   if (p.match_bits != nullptr) {
     // dense matches recorded as bits by pass 1: two blocks of 16 warps per SM
     auto kern = k_emit_bits<LAYOUT, ESIZE>;
-    const size_t sm_bytes = ((smem + 15) & ~(size_t)15) + (size_t)kEmitBitsWarps * kEmitBitsBuf * 4;
+    const size_t sm_bytes = ((smem + 15) & ~(size_t)15) + (size_t)kEmitBitsWarps * kEmitBitsRound * 2;
     cudaError_t e = raise_smem_limit(kern, sm_bytes, limits_bits);
     if (e != cudaSuccess) return e;
     const uint64_t want = (p.R + kEmitBitsWarps - 1) / kEmitBitsWarps;
