@@ -658,7 +658,7 @@ static int run_scan(const parem_dfa* dfa, const uint8_t* text, uint64_t len, uin
   sc->stats.warps_per_block = pl.R ? (uint32_t)pl.warps : 1;
   sc->stats.candidate_regs = pl.P;
   sc->stats.spec_cap_bytes = pl.spec_cap;
-  sc->stats.kernels = 1 + ((pl.R && emit) ? 1 : 0);
+  sc->stats.kernels = 1 + ((pl.R && emit) ? 1 : 0) + (bits ? 1 : 0);
   sc->stats.layout = P.layout;
   sc->stats.pair_hot_states = P.layout == kClassPair ? P.pair_hot : 0u;
   if (timed) PAREM_CUDA_TRY(cudaEventRecord(sc->ev[0], stream));

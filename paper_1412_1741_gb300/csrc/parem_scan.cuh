@@ -1734,7 +1734,9 @@ __device__ __forceinline__ void emit_row(const Tab<LAYOUT, ESIZE>& tab, const Sc
       x = tab.next(x, tab.col(ldg8(p.text + i)));
       if (x >= A) p.positions[o++] = p.pos_base + i;
     }
-  } else if (sr.flags & kPreFlag) {
+  }
+  if (sr.flags & kBitsFlag) return;  // the rest of the row comes from the match bitmap (k_emit_bits)
+  if (!(sr.flags & kHeadFlag) && (sr.flags & kPreFlag)) {
     // matches inside the merged prefix [0, t), replayed from the row's true start
     uint32_t x = sr.x;
     emit_range(tab, p, r, 0u, sr.t, x, o, end);
@@ -1777,7 +1779,8 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
        r += (uint64_t)gridDim.x * blockDim.x) {
     const SegRec& sr = p.segrec[r];
     replay = replay || (sr.count > 0 && sr.offset < p.capacity &&
-                        ((sr.flags & (kHeadFlag | kPreFlag)) || (!(sr.flags & kSlotsFlag) && sr.lv > 0)));
+                        ((sr.flags & kHeadFlag) ||
+                         (!(sr.flags & kBitsFlag) && ((sr.flags & kPreFlag) || (!(sr.flags & kSlotsFlag) && sr.lv > 0)))));
   }
   if (__syncthreads_or(replay)) {
     load_tables<LAYOUT, ESIZE>(sm, D);
@@ -1978,52 +1981,29 @@ __global__ void __launch_bounds__(1024, 1)
   publish_result(p, p.ticket + kDoneEmitWord);
 }
 
-// Dense emission from the match bitmap of pass 1: one warp per row with matches.  Lane 0
-// replays row 0's head bytes (before the aligned body, outside the bitmap); then, 1,024
-// bytes of the row at a time, every lane takes 32 bits of the bitmap, writes its positions
-// (relative to the round, 16 bits each) into a per-warp buffer in shared memory at its scan
-// offset -- two bits per step, the lowest from the front and the highest from the back --
-// and the warp writes the buffer in order with consecutive addresses.  Rows without bits
-// (a run that died inside its merged prefix, or speculation that never merged) are
-// replayed by lane 0.
+// Dense emission from the match bitmap of pass 1: one warp per row whose matches are all in
+// the bitmap, without the transition table (so more warps fit an SM).  1,024 bytes of the row
+// at a time, every lane takes 32 bits of the bitmap and writes its positions (relative to
+// the round, 16 bits each) into a per-warp buffer in shared memory at its scan offset -- two
+// bits per step, the lowest from the front and the highest from the back -- and the warp
+// writes the buffer in order with consecutive addresses.  k_emit runs after it for what
+// needs the table: row 0's head bytes (before the aligned body, outside the bitmap; their
+// positions come first, so this kernel starts row 0 after them) and the rows without bits
+// (a run that died inside its merged prefix, or speculation that never merged).
 constexpr uint32_t kEmitBitsWarps = 16;    // warps per block of k_emit_bits
 constexpr uint32_t kEmitBitsRound = 1024;  // row bytes per round (32 lanes x 32 bits)
 
-template <int LAYOUT, int ESIZE>
-__global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanParams p) {
+__global__ void __launch_bounds__(kEmitBitsWarps * 32, 3) k_emit_bits(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
-  uint8_t* const sm = smem_raw;
-  const DeviceDfa& D = p.dfa;
-  load_tables<LAYOUT, ESIZE>(sm, D);
-  __syncthreads();
-  Tab<LAYOUT, ESIZE> tab;
-  tab.sm = sm;
-  tab.gtable = D.table;
-  tab.rowbytes = D.rowbytes;
-  tab.smem_tier = 1;
-  tab.set_win(D.win);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t tbytes = Tab<LAYOUT, ESIZE>::kGlobal ? 0u : p.smem_table_bytes;
-  uint16_t* const buf = reinterpret_cast<uint16_t*>(sm + ((kTableOff + tbytes + 15u) & ~15u)) + warp * kEmitBitsRound;
+  uint16_t* const buf = reinterpret_cast<uint16_t*>(smem_raw) + warp * kEmitBitsRound;
   const uint32_t* bits32 = p.match_bits;
   const uint64_t step = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; r < p.R; r += step) {
     const SegRec sr = p.segrec[r];
-    if (sr.count == 0 || sr.offset >= p.capacity) continue;
-    if (!(sr.flags & kBitsFlag)) {
-      if (lane == 0) emit_row<LAYOUT, ESIZE>(tab, p, r);
-      continue;
-    }
+    if (sr.count == 0 || sr.offset >= p.capacity || !(sr.flags & kBitsFlag)) continue;
     const uint64_t end = (sr.offset + sr.count < p.capacity) ? sr.offset + sr.count : p.capacity;
-    uint64_t o = sr.offset;
-    if (lane == 0 && (sr.flags & kHeadFlag)) {  // row 0's bytes before the aligned body
-      uint32_t x = sr.x;
-      for (uint64_t i = 0; i < p.h && o < end; ++i) {
-        x = tab.next(x, tab.col(ldg8(p.text + i)));
-        if (x >= p.dfa.first_accept) p.positions[o++] = p.pos_base + i;
-      }
-    }
-    o = __shfl_sync(kFull, o, 0);
+    uint64_t o = sr.offset + ((sr.flags & kHeadFlag) ? sr.pre : 0u);
     const uint32_t rowlen = (uint32_t)(p.S + (r == p.R - 1 ? p.tail : 0));
     const uint64_t rword = (r * p.S) / 32;              // bitmap word of the row's first byte
     const uint64_t gpos = p.pos_base + p.h + r * p.S;   // text position of the row's first byte
@@ -2065,7 +2045,6 @@ __global__ void __launch_bounds__(kEmitBitsWarps * 32) k_emit_bits(const ScanPar
       o += total;
     }
   }
-  publish_result(p, p.ticket + kDoneEmitWord);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2268,19 +2247,18 @@ cudaError_t launch_spec_scan(const CUtensorMap& tmap, const ScanParams& p, int g
 template <int LAYOUT, int ESIZE>
 cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, int block, size_t smem,
                         cudaStream_t stream) {
-  static std::atomic<size_t> limits[64], limits_stream[64], limits_bits[64];
+  static std::atomic<size_t> limits[64], limits_stream[64];
   // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
   static std::atomic<uint64_t> choice[64];
   if (p.match_bits != nullptr) {
-    // dense matches recorded as bits by pass 1: two blocks of 16 warps per SM
-    auto kern = k_emit_bits<LAYOUT, ESIZE>;
-    const size_t sm_bytes = ((smem + 15) & ~(size_t)15) + (size_t)kEmitBitsWarps * kEmitBitsRound * 2;
-    cudaError_t e = raise_smem_limit(kern, sm_bytes, limits_bits);
-    if (e != cudaSuccess) return e;
+    // dense matches recorded as bits by pass 1: three blocks of 16 warps per SM expand them;
+    // k_emit below then writes what needs the table (row 0's head, rows without bits)
+    const size_t sm_bytes = (size_t)kEmitBitsWarps * kEmitBitsRound * 2;
     const uint64_t want = (p.R + kEmitBitsWarps - 1) / kEmitBitsWarps;
-    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid * 2, want));
-    kern<<<blocks, kEmitBitsWarps * 32, sm_bytes, stream>>>(p);
-    return cudaGetLastError();
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid * 3, want));
+    k_emit_bits<<<blocks, kEmitBitsWarps * 32, sm_bytes, stream>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   if (p.stream_emit && tm != nullptr) {
     // dense matches: pass 1's launch shape (one block per SM, warps as shared memory allows)
