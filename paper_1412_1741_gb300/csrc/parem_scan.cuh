@@ -1993,7 +1993,7 @@ __global__ void __launch_bounds__(1024, 1)
 constexpr uint32_t kEmitBitsWarps = 16;    // warps per block of k_emit_bits
 constexpr uint32_t kEmitBitsRound = 1024;  // row bytes per round (32 lanes x 32 bits)
 
-__global__ void __launch_bounds__(kEmitBitsWarps * 32, 3) k_emit_bits(const ScanParams p) {
+static __global__ void __launch_bounds__(kEmitBitsWarps * 32, 3) k_emit_bits(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint16_t* const buf = reinterpret_cast<uint16_t*>(smem_raw) + warp * kEmitBitsRound;
