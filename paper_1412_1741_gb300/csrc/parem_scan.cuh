@@ -1993,7 +1993,7 @@ __global__ void __launch_bounds__(1024, 1)
 constexpr uint32_t kEmitBitsWarps = 16;    // warps per block of k_emit_bits
 constexpr uint32_t kEmitBitsRound = 1024;  // row bytes per round (32 lanes x 32 bits)
 
-static __global__ void __launch_bounds__(kEmitBitsWarps * 32, 3) k_emit_bits(const ScanParams p) {
+static __global__ void __launch_bounds__(kEmitBitsWarps * 32, 4) k_emit_bits(const ScanParams p) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint16_t* const buf = reinterpret_cast<uint16_t*>(smem_raw) + warp * kEmitBitsRound;
@@ -2251,11 +2251,11 @@ cudaError_t launch_emit(const ScanParams& p, const CUtensorMap* tm, int grid, in
   // the chosen block size per (device, shared memory size), packed as smem << 24 | blocks << 12 | block
   static std::atomic<uint64_t> choice[64];
   if (p.match_bits != nullptr) {
-    // dense matches recorded as bits by pass 1: three blocks of 16 warps per SM expand them;
+    // dense matches recorded as bits by pass 1: four blocks of 16 warps per SM expand them;
     // k_emit below then writes what needs the table (row 0's head, rows without bits)
     const size_t sm_bytes = (size_t)kEmitBitsWarps * kEmitBitsRound * 2;
     const uint64_t want = (p.R + kEmitBitsWarps - 1) / kEmitBitsWarps;
-    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid * 3, want));
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)grid * 4, want));
     k_emit_bits<<<blocks, kEmitBitsWarps * 32, sm_bytes, stream>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
