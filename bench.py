@@ -382,6 +382,18 @@ def batch_measure(args, rank, world, dev, dist):
     step_ms = sorted(a.elapsed_time(b) for a, b in evs)
     res = batch.results()
     segs = batch.segments()
+    cfgs = batch.configs()
+    # what the autotuner chose for each DFA (its longest rows; shorter texts get one row)
+    per_dfa = []
+    for d in range(len(dfas)):
+        mine = [c for i, c in enumerate(cfgs) if i % len(dfas) == d and c["segment_bytes"]]
+        if not mine:
+            continue
+        info = pm.parem_dfa_get_info(dfas[d])
+        per_dfa.append({"dfa": d, "states": info.compact_states, "max_candidates": info.max_candidates,
+                        "segment_bytes": max(c["segment_bytes"] for c in mine), "spec": mine[0]["spec"],
+                        "table": "smem" if mine[0]["smem_table"] else "l2"})
+    tuned = {"warps_per_block": cfgs[0]["warps_per_block"], "per_dfa": per_dfa}
     # plain: one parem_match per text on the same stream (same texts)
     for i in range(min(64, n_texts)):
         pm.parem_match(items[i][0], items[i][1], length=items[i][2])
@@ -419,6 +431,7 @@ def batch_measure(args, rank, world, dev, dist):
             "batched_vs_plain": {"batched_gbs": round(value / world, 2), "plain_gbs": round(plain_gbs, 2),
                                  "speedup": round(value / world / plain_gbs, 2), "plain_calls": n_texts,
                                  "results_agree": agree},
+            "autotuned": tuned,
             "parity": {"ok": not bad, "checked": f"all {n_texts} items: final state and match count vs the oracle",
                        "mismatched_items": bad[:8]},
             "cpu_baseline": {"value": round(total / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
@@ -711,7 +724,8 @@ def run_ours(args, rank, world, local_rank):
                                         text_bytes=b["config"]["text_bytes"], dfas=b["config"]["dfas"],
                                         p50_ms=b["p50_ms"], plan_seconds_with_autotune=b["config"]["plan_seconds_with_autotune"],
                                         parity=b["parity"], cpu_baseline=b["cpu_baseline"], clocks=b["clocks"],
-                                        gpu_launches=b["gpu_launches"], roofline_frac=b["roofline"]["frac"])
+                                        gpu_launches=b["gpu_launches"], roofline_frac=b["roofline"]["frac"],
+                                        autotuned=b["autotuned"])
         line["gpu_launches"] += b["gpu_launches"]
         v = serve_measure(args, rank, world, dev)
         line["serving"] = dict(v["serving"], p50_ms=v["p50_ms"], p99_ms=v["p99_ms"], gbs=v["value"],

@@ -354,15 +354,40 @@ typedef struct {
   uint64_t capacity;      /* slots in positions */
 } parem_batch_item;
 
+/* Speculation form of a batch DFA (Algorithm 1's speculation step over the candidate set of
+ * each row; the forms differ only in how a warp holds and merges the candidates):
+ *   GROUPED      a few lanes per row hold its candidates, 32/G rows at once (sets of <= 32)
+ *   WARP         one row at a time, candidates over 32 lanes x 8 registers, merged by
+ *                warp votes on equal states (sets of <= 256)
+ *   WARP_BITMAP  one row at a time, merged through a bitmap of the states in shared memory
+ *                (any set size; DFAs of at most 16,384 states)
+ * AUTO (0) picks by the candidate-set size and the DFA's estimated synchronisation length. */
+#define PAREM_BATCH_SPEC_AUTO 0u
+#define PAREM_BATCH_SPEC_GROUPED 1u
+#define PAREM_BATCH_SPEC_WARP 2u
+#define PAREM_BATCH_SPEC_WARP_BITMAP 3u
+
 typedef struct {
-  uint32_t autotune;        /* 1: choose each DFA's segment size by timing candidates on its own
-                               items (several trial runs during parem_batch_create) */
-  uint32_t warps_per_block; /* 0 = 24 */
+  uint32_t autotune;        /* 1: choose each DFA's segment size and speculation form by timing
+                               candidates on its own items, and the block shape by timing the
+                               whole batch (several trial runs during parem_batch_create) */
+  uint32_t warps_per_block; /* 0 = 24; 1..16 = 16 warps (128 registers each); > 16 = 24 (80) */
   uint64_t segment_bytes;   /* 0 = planner/autotuner; else the same S for every item */
   uint32_t use_graph;       /* 0: launch the kernels directly in parem_batch_run; else (default
                                when the struct is NULL) replay the captured CUDA graph */
-  uint32_t reserved;
+  uint32_t spec;            /* PAREM_BATCH_SPEC_*: the form for every DFA where it applies
+                               (others keep AUTO's); not AUTO also stops the autotuner trying
+                               forms */
 } parem_batch_opts;
+
+/* The configuration a batch chose for one item (planner or autotuner). */
+typedef struct {
+  uint64_t segment_bytes;   /* S (0: the text is shorter than one row) */
+  uint32_t spec;            /* PAREM_BATCH_SPEC_GROUPED, _WARP or _WARP_BITMAP */
+  uint32_t warps_per_block; /* of the whole batch's launch: 16 or 24 */
+  uint32_t smem_table;      /* 1: the DFA's table is staged in shared memory, 0: read from L2 */
+  uint32_t reserved;
+} parem_batch_config;
 
 /* Plan a batch of n_items items (host array, copied) on the current device.  Errors:
  * INVALID_ARG, OOM, CUDA. */
@@ -378,6 +403,10 @@ int parem_batch_results(const parem_batch* batch, parem_result* out);
 
 /* Segment size chosen for item i (planner or autotuner).  Errors: INVALID_ARG. */
 int parem_batch_item_segment(const parem_batch* batch, uint32_t i, uint64_t* segment_bytes);
+
+/* Everything chosen for item i (given order): segment size, speculation form, block shape,
+ * table tier.  Errors: INVALID_ARG. */
+int parem_batch_item_config(const parem_batch* batch, uint32_t i, parem_batch_config* out);
 
 /* Counters of the last run summed over the batch's items (the plan fields are 0; unmerged
  * rows, longest merge, kernels and the cycle counters are filled).  Errors: INVALID_ARG. */

@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = [
     "parem_load_dfa", "parem_prepare_info", "parem_dfa_get_info", "parem_free_dfa", "parem_pair_preview", "parem_match",
     "parem_match_ex", "parem_match_host", "parem_release_scratch", "parem_strerror", "parem_version",
     "parem_last_stats", "parem_match_noalloc", "parem_batch_create", "parem_batch_run", "parem_batch_results",
-    "parem_batch_item_segment", "parem_batch_stats", "parem_batch_free", "parem_server_create", "parem_server_submit",
+    "parem_batch_item_segment", "parem_batch_item_config", "parem_batch_stats", "parem_batch_free", "parem_server_create", "parem_server_submit",
     "parem_server_poll", "parem_server_drain", "parem_server_replay", "parem_server_get_stats",
     "parem_server_free", "parem_clock_ns", "parem_regex_compile", "parem_regex_info", "parem_regex_export",
     "parem_regex_load", "parem_regex_free",
@@ -462,12 +462,25 @@ class _BatchItem(ctypes.Structure):
                 ("positions", ctypes.c_void_p), ("capacity", ctypes.c_uint64)]
 
 
+# speculation forms of a batch DFA (parem_batch_opts.spec, parem_batch_config.spec)
+PAREM_BATCH_SPEC_AUTO = 0
+PAREM_BATCH_SPEC_GROUPED = 1
+PAREM_BATCH_SPEC_WARP = 2
+PAREM_BATCH_SPEC_WARP_BITMAP = 3
+BATCH_SPEC_NAMES = {1: "grouped", 2: "warp", 3: "warp_bitmap"}
+
+
 class BatchOpts(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
-                ("segment_bytes", ctypes.c_uint64), ("use_graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("segment_bytes", ctypes.c_uint64), ("use_graph", ctypes.c_uint32), ("spec", ctypes.c_uint32)]
 
-    def __init__(self, autotune=0, warps_per_block=0, segment_bytes=0, use_graph=1):
-        super().__init__(autotune, warps_per_block, segment_bytes, use_graph, 0)
+    def __init__(self, autotune=0, warps_per_block=0, segment_bytes=0, use_graph=1, spec=PAREM_BATCH_SPEC_AUTO):
+        super().__init__(autotune, warps_per_block, segment_bytes, use_graph, spec)
+
+
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("segment_bytes", ctypes.c_uint64), ("spec", ctypes.c_uint32), ("warps_per_block", ctypes.c_uint32),
+                ("smem_table", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 def _bind_batch(lib):
@@ -483,6 +496,8 @@ def _bind_batch(lib):
     lib.parem_batch_results.restype = ctypes.c_int
     lib.parem_batch_item_segment.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint64)]
     lib.parem_batch_item_segment.restype = ctypes.c_int
+    lib.parem_batch_item_config.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(_BatchConfig)]
+    lib.parem_batch_item_config.restype = ctypes.c_int
     lib.parem_batch_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.parem_batch_stats.restype = ctypes.c_int
     lib.parem_batch_free.argtypes = [vp]
@@ -520,6 +535,20 @@ class Batch:
         for i in range(self.n):
             lib.parem_batch_item_segment(self._h, i, ctypes.byref(v))
             out.append(v.value)
+        return out
+
+    def configs(self):
+        """Per item (given order): the segment size, speculation form, block shape and table
+        tier the batch chose."""
+        lib = load_library()
+        out = []
+        c = _BatchConfig()
+        for i in range(self.n):
+            rc = lib.parem_batch_item_config(self._h, i, ctypes.byref(c))
+            if rc != PAREM_OK:
+                raise ParemError(rc, "parem_batch_item_config")
+            out.append({"segment_bytes": c.segment_bytes, "spec": BATCH_SPEC_NAMES.get(c.spec, str(c.spec)),
+                        "warps_per_block": c.warps_per_block, "smem_table": bool(c.smem_table)})
         return out
 
     def stats(self) -> dict:

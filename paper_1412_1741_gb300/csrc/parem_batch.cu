@@ -1,10 +1,13 @@
 // parem_batch.cu -- batched matching: many (text, DFA) items in one persistent launch, the
-// whole run captured in a CUDA graph; a per-DFA segment-size autotuner.
+// whole run captured in a CUDA graph; an autotuner for each DFA's segment size and
+// speculation form and for the batch's block shape.
 //
 // Planning (parem_batch_create):
 //   * every DFA of the batch gets its batch-kernel copy (u16 class table, u16 column map);
 //   * items are grouped by DFA ("slots"); each item gets rows of S bytes (per-DFA S from the
-//     autotuner, or the planner's default: about two rows per lane of the whole GPU);
+//     autotuner, or the planner's default: about two rows per lane of the whole GPU); each
+//     slot gets a speculation form (grouped, warp-wide in registers, warp-wide through a
+//     state bitmap);
 //   * texts shorter than one 64-byte row go to a one-thread-per-item kernel;
 //   * one scratch allocation holds every item's status words, row records, recorded positions,
 //     slot maps and result word; one descriptor allocation holds the per-item scan parameters
@@ -38,6 +41,8 @@ struct parem_batch {
   std::vector<uint32_t> order;          // sorted position -> given index
   std::vector<uint64_t> seg;            // per given item: S (0 for texts shorter than a row)
   std::vector<uint32_t> cap;            // per given item: speculation cap (bytes)
+  std::vector<uint32_t> spec;           // per given item: speculation form (PAREM_BATCH_SPEC_*)
+  std::vector<uint8_t> smem_table;      // per given item: its DFA's table is in shared memory
   void* desc = nullptr;
   void* scratch = nullptr;
   DevResult* host_res = nullptr;        // pinned, per sorted item
@@ -162,21 +167,39 @@ int enqueue(parem_batch* b, cudaStream_t st) {
   return PAREM_OK;
 }
 
+// The speculation form a DFA gets in a batch: `want` where it applies, else the default
+// (grouped for candidate sets of one warp or less; the state bitmap for sets beyond the
+// registers, or for DFAs of many states that synchronise slowly; else registers).
+uint32_t resolve_spec(const parem_dfa* d, uint32_t want) {
+  const Prepared& P = d->host;
+  const bool bitmap_ok = P.n <= 16384;
+  if (want == PAREM_BATCH_SPEC_GROUPED && P.max_cand <= kLanes) return want;
+  if (want == PAREM_BATCH_SPEC_WARP && P.max_cand <= 8 * kLanes) return want;
+  if (want == PAREM_BATCH_SPEC_WARP_BITMAP && bitmap_ok) return want;
+  if (P.max_cand <= kLanes) return PAREM_BATCH_SPEC_GROUPED;
+  if (bitmap_ok && (P.max_cand > 8 * kLanes || (P.sync_len > 16 && P.n >= 256))) return PAREM_BATCH_SPEC_WARP_BITMAP;
+  return PAREM_BATCH_SPEC_WARP;
+}
+
 struct Slot {
   parem_dfa* dfa;
   std::vector<uint32_t> items;  // given indices
+  uint32_t spec = PAREM_BATCH_SPEC_AUTO;
   uint32_t bitmap_words = 0;
   uint32_t spec_bytes = kSpecBytes;
   bool smem_tier = false;
   double weight = 0;
 };
 
-// Plan a batch.  seg_for: per given item, the segment size to use (0 = default).  With an
-// arena, nothing is allocated: the batch lives in the arena's buffers (PAREM_ERR_TOO_LARGE
-// when it does not fit) and its descriptors are copied on the arena's stream.
+// Plan a batch.  seg_for: per given item, the segment size to use (0 = default); spec_for
+// (optional): per given item, the speculation form of its DFA (AUTO = o->spec, else the
+// default; an item's DFA takes the form of its first item).  With an arena, nothing is
+// allocated: the batch lives in the arena's buffers (PAREM_ERR_TOO_LARGE when it does not
+// fit) and its descriptors are copied on the arena's stream.
 int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch_opts* o, int grid_limit,
                     const std::vector<uint64_t>& seg_for, bool use_graph, bool keep_positions,
-                    parem_batch** out, const BatchArena* arena = nullptr) {
+                    parem_batch** out, const BatchArena* arena = nullptr,
+                    const std::vector<uint32_t>* spec_for = nullptr) {
   *out = nullptr;
   if (!items || n == 0) return PAREM_ERR_INVALID_ARG;
   int dev = -1;
@@ -204,6 +227,9 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
       it = slot_of.emplace(items[i].dfa, (uint32_t)slots.size()).first;
       Slot s;
       s.dfa = const_cast<parem_dfa*>(items[i].dfa);
+      uint32_t want = o ? o->spec : PAREM_BATCH_SPEC_AUTO;
+      if (spec_for && i < spec_for->size() && (*spec_for)[i]) want = (*spec_for)[i];
+      s.spec = resolve_spec(s.dfa, want);
       slots.push_back(s);
     }
   }
@@ -214,13 +240,14 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
       return rc;
     }
     const Prepared& P = s.dfa->host;
-    if (P.n <= 16384 && P.max_cand > kLanes && (P.max_cand > 256 || (P.sync_len > 16 && P.n >= 256))) {
+    if (s.spec == PAREM_BATCH_SPEC_WARP_BITMAP) {
       s.bitmap_words = (P.n + 31) / 32;
       s.spec_bytes = kSpecBytes + (uint32_t)up(8ull * s.bitmap_words, 16) + 512u;
     }
   }
   // launch shape and shared-memory carve-up
-  const int warps = std::min<int>(24, o && o->warps_per_block ? (int)o->warps_per_block : 24);
+  // the two block shapes of k_batch_scan
+  const int warps = (o && o->warps_per_block && o->warps_per_block <= 16) ? 16 : 24;
   uint32_t spec_bytes = kSpecBytes;
   for (const Slot& s : slots) spec_bytes = std::max(spec_bytes, s.spec_bytes);
   const uint32_t per_warp = kStages * kStageBytes + kStages * 8 + spec_bytes;
@@ -248,6 +275,8 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
   std::vector<Plan1> plan(n);
   b->seg.assign(n, 0);
   b->cap.assign(n, 0);
+  b->spec.assign(n, 0);
+  b->smem_table.assign(n, 0);
   for (uint32_t i = 0; i < n; ++i) {
     const parem_batch_item& it = items[i];
     Plan1& pl = plan[i];
@@ -272,6 +301,8 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     if (pl.cap == 0) pl.cap = 16;
     b->seg[i] = pl.R ? S : 0;
     b->cap[i] = pl.cap;
+    b->spec[i] = slots[slot_of[it.dfa]].spec;
+    b->smem_table[i] = slots[slot_of[it.dfa]].smem_tier ? 1 : 0;
     if (pl.R) slots[slot_of[it.dfa]].items.push_back(i);
   }
   // sorted order: scanned items by slot, then the short ones
@@ -391,7 +422,7 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     BatchSlot& bs = hslots[si];
     bs.dfa = slots[si].dfa->batch;
     bs.smem_tier = slots[si].smem_tier ? 1u : 0u;
-    bs.grouped = slots[si].dfa->host.max_cand <= kLanes ? 1u : 0u;
+    bs.grouped = slots[si].spec == PAREM_BATCH_SPEC_GROUPED ? 1u : 0u;
     bs.item_begin = pos_k;
     bs.item_end = pos_k + (uint32_t)slots[si].items.size();
     bs.n_chunks = slot_chunks[si];
@@ -554,15 +585,20 @@ int run_internal(parem_batch* b, cudaStream_t st) {
   return capacity ? PAREM_ERR_CAPACITY : PAREM_OK;
 }
 
-// Time one DFA's items alone with segment size S on `grid` CTAs, the DFA's share of the
-// batch's grid (trial batch without positions).
-float time_trial(const std::vector<parem_batch_item>& its, uint64_t S, int warps, int grid) {
+// Time a trial batch without positions (the best of `reps` runs after one warm-up run):
+// items with segment size S and speculation form `spec`, or (S == 0) with seg_for and
+// spec_for per item, as planned for the whole GPU.
+float time_trial(const std::vector<parem_batch_item>& its, uint64_t S, int warps, int grid, uint32_t spec,
+                 const std::vector<uint64_t>& seg_for = {}, const std::vector<uint32_t>* spec_for = nullptr,
+                 int reps = 2) {
   parem_batch_opts o{};
   o.warps_per_block = (uint32_t)warps;
   o.segment_bytes = S;
+  o.spec = spec;
   parem_batch* t = nullptr;
-  std::vector<uint64_t> none;
-  if (create_internal(its.data(), (uint32_t)its.size(), &o, grid, none, false, false, &t) != PAREM_OK) return 1e30f;
+  if (create_internal(its.data(), (uint32_t)its.size(), &o, grid, seg_for, false, false, &t, nullptr, spec_for) !=
+      PAREM_OK)
+    return 1e30f;
   cudaStream_t st;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   cudaEvent_t e0, e1;
@@ -570,7 +606,7 @@ float time_trial(const std::vector<parem_batch_item>& its, uint64_t S, int warps
   cudaEventCreate(&e1);
   float best = 1e30f;
   run_internal(t, st);  // warm-up
-  for (int rep = 0; rep < 1; ++rep) {
+  for (int rep = 0; rep < reps; ++rep) {
     cudaEventRecord(e0, st);
     if (run_internal(t, st) != PAREM_OK) {
       best = 1e30f;
@@ -597,72 +633,117 @@ extern "C" int parem_batch_create(const parem_batch_item* items, uint32_t n_item
   *out = nullptr;
   const bool graph = opts ? opts->use_graph != 0 : true;
   std::vector<uint64_t> seg_for;
-  if (opts && opts->autotune && !opts->segment_bytes && items && n_items) {
-    // per DFA: time candidate segment sizes on that DFA's own items (no positions)
+  std::vector<uint32_t> spec_for;
+  parem_batch_opts o = opts ? *opts : parem_batch_opts{};
+  if (!opts) o.use_graph = 1;
+  if (o.autotune && !o.segment_bytes && items && n_items) {
+    // Per DFA: time candidate segment sizes and speculation forms on all of that DFA's items
+    // alone on the whole GPU (no positions).  That time is the larger of the DFA's work over
+    // the GPU and its critical path (the longest chain of dependent lookups of one chunk:
+    // speculation of its 32 rows, then the longest row), and in a batch that mixes DFAs the
+    // slowest DFA's critical path is what the others cannot hide.  A change must gain 3 %.
+    // Then the whole batch: the tuned and the default plans, with 24 and with 16 warps.
     parem_batch* probe = nullptr;
-    int rc = create_internal(items, n_items, opts, 0, seg_for, false, false, &probe);
+    int rc = create_internal(items, n_items, &o, 0, seg_for, false, false, &probe);
     if (rc != PAREM_OK) return rc;
     const int warps = probe->block / 32;
-    const int grid = probe->grid;
     std::map<const parem_dfa*, std::vector<parem_batch_item>> by_dfa;
     std::map<const parem_dfa*, uint64_t> base_s;
+    std::map<const parem_dfa*, uint32_t> base_spec;
+    std::vector<uint64_t> seg_default(n_items, 0);
+    std::vector<uint32_t> spec_default(n_items, 0);
     for (uint32_t i = 0; i < n_items; ++i) {
+      seg_default[i] = probe->seg[i];
+      spec_default[i] = probe->spec[i];
       if (probe->seg[i] == 0) continue;
       parem_batch_item it = items[i];
       it.positions = nullptr;
       it.capacity = 0;
       by_dfa[items[i].dfa].push_back(it);
       base_s[items[i].dfa] = std::max(base_s[items[i].dfa], probe->seg[i]);
+      base_spec[items[i].dfa] = probe->spec[i];
     }
     release(probe);
-    std::map<const parem_dfa*, uint64_t> best_s;
-    uint64_t all_bytes = 0;
-    for (auto& kv : by_dfa)
-      for (auto& it : kv.second) all_bytes += it.len;
+    constexpr float kGain = 0.97f;
+    std::map<const parem_dfa*, std::pair<uint64_t, uint32_t>> best_of;
     for (auto& kv : by_dfa) {
+      const parem_dfa* d = kv.first;
       uint64_t bytes = 0;
       for (auto& it : kv.second) bytes += it.len;
-      const uint64_t s0 = base_s[kv.first];
+      const uint64_t s0 = base_s[d];
+      const uint32_t f0 = base_spec[d];
       if (bytes < (4u << 20)) {
-        best_s[kv.first] = s0;
+        best_of[d] = {s0, f0};
         continue;
       }
-      // trials on the DFA's first items up to 64 MiB, with the matching share of the batch's
-      // CTAs (the DFA's bytes over all bytes)
-      std::vector<parem_batch_item> sub;
-      uint64_t sub_bytes = 0;
-      for (const auto& it : kv.second) {
-        if (sub_bytes >= (64u << 20)) break;
-        sub.push_back(it);
-        sub_bytes += it.len;
-      }
-      const int share = std::max(1, (int)std::lround((double)grid * (double)sub_bytes / (double)all_bytes));
-      // a first trial at the default size teaches the DFA's convergence length
-      float best = time_trial(sub, s0, warps, share);
-      uint64_t pick = s0;
-      const uint64_t smin = min_row_bytes(kv.first, 8);
-      const uint64_t smax = std::max(smin, max_row_bytes(kv.first, kv.first->host.max_cand));
-      std::vector<uint64_t> tried{s0};
-      for (double f : {0.5, 1.0, 2.0, 4.0}) {
-        uint64_t S = up((uint64_t)std::llround((double)std::max(s0, smin) * f), kBox);
-        S = std::min<uint64_t>(std::max<uint64_t>(S, smin), std::min<uint64_t>(smax, 4u << 20));
-        if (std::find(tried.begin(), tried.end(), S) != tried.end()) continue;
-        tried.push_back(S);
-        const float ms = time_trial(sub, S, warps, share);
-        if (ms < best) {
+      // a first trial at the default size and form teaches the DFA's convergence length
+      float best = time_trial(kv.second, s0, warps, 0, f0);
+      uint64_t pick_s = s0;
+      uint32_t pick_f = f0;
+      // sizes from a quarter to four times the default, no shorter than the longest merge
+      // seen so far (plus a quarter) nor than 1 KiB: shorter rows than the planner's default
+      // (several merge lengths) cost more speculation per byte but shorten each chunk
+      const uint64_t conv = d->conv_hint.load();
+      const uint64_t smin = std::max<uint64_t>(1024, up(conv + conv / 4, kBox));
+      const uint64_t smax = std::max(smin, std::min<uint64_t>(max_row_bytes(d, d->host.max_cand), 4u << 20));
+      auto clamp_s = [&](double v) {
+        return std::min<uint64_t>(std::max<uint64_t>(up((uint64_t)std::llround(v), kBox), smin), smax);
+      };
+      std::vector<std::pair<uint64_t, uint32_t>> tried{{s0, f0}};
+      auto trial = [&](uint64_t S, uint32_t f) {
+        if (std::find(tried.begin(), tried.end(), std::make_pair(S, f)) != tried.end()) return;
+        tried.push_back({S, f});
+        const float ms = time_trial(kv.second, S, warps, 0, f);
+        if (ms < best * kGain) {
           best = ms;
-          pick = S;
+          pick_s = S;
+          pick_f = f;
         }
+      };
+      for (double g : {0.25, 0.5, 2.0, 4.0}) trial(clamp_s((double)s0 * g), f0);
+      // the other forms that apply to this DFA, around the best size so far
+      const uint64_t s1 = pick_s;
+      for (uint32_t f : {PAREM_BATCH_SPEC_GROUPED, PAREM_BATCH_SPEC_WARP, PAREM_BATCH_SPEC_WARP_BITMAP}) {
+        if (f == f0 || resolve_spec(d, f) != f) continue;
+        for (double g : {1.0, 0.5, 2.0}) trial(clamp_s((double)s1 * g), f);
       }
-      best_s[kv.first] = pick;
+      best_of[d] = {pick_s, pick_f};
     }
-    seg_for.assign(n_items, 0);
+    std::vector<uint64_t> seg_tuned(n_items, 0);
+    std::vector<uint32_t> spec_tuned(n_items, 0);
     for (uint32_t i = 0; i < n_items; ++i) {
-      auto it = best_s.find(items[i].dfa);
-      if (it != best_s.end()) seg_for[i] = it->second;
+      auto it = best_of.find(items[i].dfa);
+      if (it != best_of.end()) {
+        seg_tuned[i] = it->second.first;
+        spec_tuned[i] = it->second.second;
+      }
     }
+    // the whole batch: tuned against default plans, and the block shape (unless given)
+    std::vector<parem_batch_item> all(items, items + n_items);
+    for (auto& it : all) {
+      it.positions = nullptr;
+      it.capacity = 0;
+    }
+    float best = 1e30f;
+    bool tuned = true;
+    int pick_w = warps;
+    for (int w : {24, 16}) {
+      if (o.warps_per_block && w != warps) continue;
+      const float tt = time_trial(all, 0, w, 0, PAREM_BATCH_SPEC_AUTO, seg_tuned, &spec_tuned, 3);
+      const float td = time_trial(all, 0, w, 0, PAREM_BATCH_SPEC_AUTO, seg_default, &spec_default, 3);
+      // the first shape tried is the default; another must gain 3 %
+      const float scale = best < 1e29f ? kGain : 1.0f;
+      if (std::min(tt, td) < best * scale) {
+        best = std::min(tt, td);
+        tuned = tt <= td;
+        pick_w = w;
+      }
+    }
+    seg_for = tuned ? seg_tuned : seg_default;
+    spec_for = tuned ? spec_tuned : spec_default;
+    o.warps_per_block = (uint32_t)pick_w;
   }
-  return create_internal(items, n_items, opts, 0, seg_for, graph, true, out);
+  return create_internal(items, n_items, &o, 0, seg_for, graph, true, out, nullptr, &spec_for);
 }
 
 extern "C" int parem_batch_run(parem_batch* batch, void* stream) {
@@ -717,6 +798,16 @@ extern "C" int parem_batch_stats(const parem_batch* batch, parem_stats* out) {
 extern "C" int parem_batch_item_segment(const parem_batch* batch, uint32_t i, uint64_t* segment_bytes) {
   if (!batch || !segment_bytes || i >= batch->n_items) return PAREM_ERR_INVALID_ARG;
   *segment_bytes = batch->seg[i];
+  return PAREM_OK;
+}
+
+extern "C" int parem_batch_item_config(const parem_batch* batch, uint32_t i, parem_batch_config* out) {
+  if (!batch || !out || i >= batch->n_items) return PAREM_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->segment_bytes = batch->seg[i];
+  out->spec = batch->spec[i];
+  out->warps_per_block = (uint32_t)(batch->block / 32);
+  out->smem_table = batch->smem_table[i];
   return PAREM_OK;
 }
 

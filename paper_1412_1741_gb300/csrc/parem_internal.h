@@ -31,7 +31,7 @@ constexpr uint64_t kMaxText = 1ull << 45;
 // map; its entries are u8 when every column offset fits a byte, else u16 (the *W layouts).
 enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClassSmemW = 3, kClassGlobalW = 4,
                          // batch kernels: class-indexed u16 table with a u16 column map, staged in
-                         // shared memory or read from global memory as each DFA requires
+                         // shared memory
                          kBatchDyn = 5,
                          // byte-indexed table plus a 4-symbol-stride table for the main run (small
                          // DFAs whose bytes 0..K-2 are distinct classes and all others one class)
@@ -41,7 +41,10 @@ enum Layout : uint32_t { kByteSmem = 0, kClassSmem = 1, kClassGlobal = 2, kClass
                          kClassWin = 7,
                          // kClassWin plus a two-byte stride table over the hot states for the main
                          // run (texts of lowercase letters and spaces; see the pair table below)
-                         kClassPair = 8 };
+                         kClassPair = 8,
+                         // batch kernels: the kBatchDyn copy read from global memory (L2), for
+                         // DFAs whose table does not fit the shared memory the stages leave
+                         kBatchGlobal = 9 };
 // Two-byte stride ("pair") table of kClassPair.  A byte b of {0x20, 0x61..0x7A} has the code
 // f = b & 0x1F (0 for the space, 1..26 for a..z); two bytes form the pair index 27 f0 + f1.
 // The hot states are the compact states 0 .. H-1 (non-accepting, the most visited ones); row

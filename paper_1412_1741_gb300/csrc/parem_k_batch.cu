@@ -6,9 +6,20 @@
 namespace parem {
 
 cudaError_t launch_batch_scan(const BatchParams& bp, int grid, int block, size_t smem, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_batch_scan<<<grid, block, smem, s>>>(bp);
+  // two block shapes: 24 warps at 80 registers, or 16 warps at 128
+  if (block == 768) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_batch_scan<768>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_scan<768><<<grid, block, smem, s>>>(bp);
+  } else if (block == 512) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_batch_scan<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_scan<512><<<grid, block, smem, s>>>(bp);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

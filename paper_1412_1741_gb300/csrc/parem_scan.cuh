@@ -148,14 +148,13 @@ __device__ __forceinline__ bool wait_expired(const DevResult* r, uint64_t budget
 template <int LAYOUT, int ESIZE>
 struct Tab {
   static constexpr bool kByte = LAYOUT == kByteSmem || LAYOUT == kByteStride;
-  static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW;
-  static constexpr bool kDyn = LAYOUT == kBatchDyn;
-  static constexpr bool kWide = LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW || LAYOUT == kBatchDyn;
+  static constexpr bool kGlobal = LAYOUT == kClassGlobal || LAYOUT == kClassGlobalW || LAYOUT == kBatchGlobal;
+  static constexpr bool kWide =
+      LAYOUT == kClassSmemW || LAYOUT == kClassGlobalW || LAYOUT == kBatchDyn || LAYOUT == kBatchGlobal;
   static constexpr bool kWin = LAYOUT == kClassWin || LAYOUT == kClassPair;
   const uint8_t* sm;       // dynamic shared memory base
   const uint8_t* gtable;   // global table (global layouts)
   uint32_t rowbytes;
-  uint32_t smem_tier;      // kBatchDyn: 1 when the table is staged in shared memory
   // kClassWin, from the window [lo, lo + w) and the extra byte xb: 2 * (2 - lo) (mod 2^32),
   // 2 * (w + 2) and 2 * (w + 3) (column byte offsets for 2-byte entries), and xb
   uint32_t win_k, win_cap, win_xcol, win_xb;
@@ -181,7 +180,7 @@ struct Tab {
   }
   __device__ __forceinline__ uint32_t next(uint32_t s, uint32_t c) const {
     const uint32_t o = s * rowbytes + c;
-    if (kGlobal || (kDyn && !smem_tier)) {
+    if (kGlobal) {
       return ESIZE == 1 ? (uint32_t)__ldg(gtable + o)
                         : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(gtable + o));
     }
@@ -1647,7 +1646,6 @@ __global__ void __launch_bounds__(spec_scan_threads<LAYOUT, P>(), 1)
   tab.sm = sm;
   tab.gtable = p.dfa.table;
   tab.rowbytes = p.dfa.rowbytes;
-  tab.smem_tier = 1;
   tab.set_win(p.dfa.win);
   for (;;) {
     uint32_t ticket = 0;
@@ -1790,7 +1788,6 @@ __global__ void __launch_bounds__(1024) k_emit(const ScanParams p) {
   tab.sm = sm;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
-  tab.smem_tier = 1;
   tab.set_win(p.dfa.win);
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < p.R;
        r += (uint64_t)gridDim.x * blockDim.x)
@@ -1832,7 +1829,6 @@ __global__ void __launch_bounds__(1024, 1)
   tab.sm = sm;
   tab.gtable = p.dfa.table;
   tab.rowbytes = p.dfa.rowbytes;
-  tab.smem_tier = 1;
   tab.set_win(p.dfa.win);
   const uint32_t A = p.dfa.first_accept;
   const uint32_t nblk = (uint32_t)(p.S / kBox);
@@ -2063,7 +2059,6 @@ __global__ void k_tiny(const ScanParams p) {
   tab.sm = sm;
   tab.gtable = D.table;
   tab.rowbytes = D.rowbytes;
-  tab.smem_tier = 1;
   tab.set_win(p.dfa.win);
   uint32_t x = p.init_state;
   uint64_t cnt = 0;
@@ -2092,7 +2087,23 @@ __global__ void k_tiny(const ScanParams p) {
 // another slot that still has chunks.  Within a slot the chunk protocol is the one of
 // k_spec_scan, per item.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ BatchParams bp) {
+// One chunk of a batch item, with the slot's table tier (shared memory or global) and
+// speculation form (grouped, or warp-wide over P registers) fixed at compile time.  Not
+// inlined: each form gets its own register allocation under the kernel's launch bound.
+template <int LAYOUT, int P>
+__device__ __noinline__ void batch_chunk(WarpCtx& wc, uint8_t* sm, const BatchSlot& S, const BatchItem& it,
+                                         uint64_t j) {
+  Tab<LAYOUT, 2> tab;
+  tab.sm = sm;
+  tab.gtable = S.dfa.table;
+  tab.rowbytes = S.dfa.rowbytes;
+  tab.set_win(0);
+  scan_chunk<LAYOUT, 2, P>(wc, tab, it.p, &it.tmap, j);
+}
+
+// THREADS: 768 (24 warps at 80 registers) or 512 (16 warps at 128 registers).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_batch_scan(const __grid_constant__ BatchParams bp) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ uint32_t s_next;
   uint8_t* const sm = smem_raw;
@@ -2122,12 +2133,6 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
     const BatchSlot& S = bp.slots[slot];
     load_tables_dyn(sm, S.dfa, S.smem_tier);
     __syncthreads();
-    Tab<kBatchDyn, 2> tab;
-    tab.sm = sm;
-    tab.gtable = S.dfa.table;
-    tab.rowbytes = S.dfa.rowbytes;
-    tab.smem_tier = S.smem_tier;
-    tab.set_win(0);
     for (;;) {
       uint32_t ticket = 0;
       if (lane == 0) ticket = atomicAdd(S.ticket, 1u);
@@ -2141,10 +2146,18 @@ __global__ void __launch_bounds__(768, 1) k_batch_scan(const __grid_constant__ B
       }
       const BatchItem& it = bp.items[lo];
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it.tmap) : "memory");
-      if (S.grouped)
-        scan_chunk<kBatchDyn, 2, 1>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
-      else
-        scan_chunk<kBatchDyn, 2, 8>(wc, tab, it.p, &it.tmap, ticket - it.chunk_base);
+      const uint64_t j = ticket - it.chunk_base;
+      if (S.smem_tier) {
+        if (S.grouped)
+          batch_chunk<kBatchDyn, 1>(wc, sm, S, it, j);
+        else
+          batch_chunk<kBatchDyn, 8>(wc, sm, S, it, j);
+      } else {
+        if (S.grouped)
+          batch_chunk<kBatchGlobal, 1>(wc, sm, S, it, j);
+        else
+          batch_chunk<kBatchGlobal, 8>(wc, sm, S, it, j);
+      }
       flush_cycles(wc, it.p.result);  // items differ from chunk to chunk
     }
     __syncthreads();  // every warp is done with this slot's tables
@@ -2173,11 +2186,6 @@ __global__ void __launch_bounds__(256) k_batch_emit(const __grid_constant__ Batc
   const BatchSlot& S = bp.slots[slot];
   load_tables_dyn(sm, S.dfa, S.smem_tier);
   __syncthreads();
-  Tab<kBatchDyn, 2> tab;
-  tab.sm = sm;
-  tab.gtable = S.dfa.table;
-  tab.rowbytes = S.dfa.rowbytes;
-  tab.smem_tier = S.smem_tier;
   const uint64_t rr = bp.emit_row0[blockIdx.x] + threadIdx.x;
   if (rr >= S.n_rows) return;
   uint32_t lo = S.item_begin, hi = S.item_end - 1;
@@ -2187,7 +2195,19 @@ __global__ void __launch_bounds__(256) k_batch_emit(const __grid_constant__ Batc
   }
   const BatchItem& it = bp.items[lo];
   if (it.p.segrec == nullptr || it.p.R == 0) return;
-  emit_row<kBatchDyn, 2>(tab, it.p, rr - it.row_base);
+  if (S.smem_tier) {
+    Tab<kBatchDyn, 2> tab;
+    tab.sm = sm;
+    tab.gtable = S.dfa.table;
+    tab.rowbytes = S.dfa.rowbytes;
+    emit_row<kBatchDyn, 2>(tab, it.p, rr - it.row_base);
+  } else {
+    Tab<kBatchGlobal, 2> tab;
+    tab.sm = sm;
+    tab.gtable = S.dfa.table;
+    tab.rowbytes = S.dfa.rowbytes;
+    emit_row<kBatchGlobal, 2>(tab, it.p, rr - it.row_base);
+  }
 }
 
 // Batch items too short for one row: one thread per item.

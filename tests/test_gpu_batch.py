@@ -106,3 +106,59 @@ def test_batch_autotuner_and_forced_segments(torch):
     batch.run()
     _check(batch, items, want)
     batch.free()
+
+
+def _expected_form(info, forced):
+    """The speculation form a batch gives a DFA when `forced` is asked for: the forced form
+    where it applies (grouped: candidate sets of at most 32 states; registers: at most 256;
+    the state bitmap: DFAs of at most 16,384 states), else the default's."""
+    m, n = info.max_candidates, info.compact_states
+    if forced == pm.PAREM_BATCH_SPEC_GROUPED and m <= 32:
+        return "grouped"
+    if forced == pm.PAREM_BATCH_SPEC_WARP and m <= 256:
+        return "warp"
+    if forced == pm.PAREM_BATCH_SPEC_WARP_BITMAP and n <= 16384:
+        return "warp_bitmap"
+    return None
+
+
+@pytest.mark.parametrize("warps", [16, 24])
+@pytest.mark.parametrize("form", [pm.PAREM_BATCH_SPEC_GROUPED, pm.PAREM_BATCH_SPEC_WARP,
+                                  pm.PAREM_BATCH_SPEC_WARP_BITMAP])
+def test_batch_speculation_forms_and_block_shapes_against_the_oracle(torch, form, warps):
+    """Each speculation form and block shape, forced on every DFA where it applies, gives
+    every item the oracle's final state, count and positions; the batch reports the form,
+    shape and segment size it used."""
+    dfas, texts, items, want = _make(torch, n_items=16, seed=11, max_len=300_000)
+    batch = pm.parem_batch_create(items, pm.BatchOpts(spec=form, warps_per_block=warps))
+    batch.run()
+    cfgs = batch.configs()
+    segs = batch.segments()
+    for (dfa, view, pos), r, (ref, ref_pos, spec, text), c, s in zip(items, batch.results(), want, cfgs, segs):
+        o = oracle.scan(spec.table, spec.byte_to_symbol, spec.start, spec.accept, text)
+        assert (r.final_state, r.match_count) == (o.final_state, o.match_count)
+        if pos is not None:
+            assert np.array_equal(pos[: r.n_written].cpu().numpy().astype(np.uint64), o.positions)
+        assert c["warps_per_block"] == warps and c["segment_bytes"] == s
+        exp = _expected_form(pm.parem_dfa_get_info(dfa), form)
+        if exp is not None:
+            assert c["spec"] == exp
+        else:
+            assert c["spec"] in ("grouped", "warp", "warp_bitmap")
+    batch.free()
+
+
+def test_batch_autotuner_reports_one_form_per_dfa(torch):
+    """The autotuner's choice: one speculation form per DFA, one block shape for the batch,
+    and results equal to the per-item scans."""
+    dfas, texts, items, want = _make(torch, n_items=30, seed=9, max_len=4 << 20)
+    batch = pm.parem_batch_create(items, pm.BatchOpts(autotune=1))
+    batch.run()
+    _check(batch, items, want)
+    cfgs = batch.configs()
+    assert len({c["warps_per_block"] for c in cfgs}) == 1 and cfgs[0]["warps_per_block"] in (16, 24)
+    form_of = {}
+    for (dfa, _, _), c in zip(items, cfgs):
+        if c["segment_bytes"]:
+            assert form_of.setdefault(id(dfa), c["spec"]) == c["spec"]
+    batch.free()
