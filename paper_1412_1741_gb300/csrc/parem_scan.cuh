@@ -420,38 +420,107 @@ struct RowAhead<false> {
   __device__ __forceinline__ void shift(const uint8_t*, uint32_t, uint32_t) {}
 };
 
-template <int LAYOUT, int ESIZE, int P>
-__device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p,
-                                           const CUtensorMap* tmap, const uint64_t j) {
-  uint8_t* const sm = wc.sm;
-  const uint32_t lane = wc.lane, stage0 = wc.stage0, bar0 = wc.bar0;
-  uint16_t* const hand = wc.hand;
-  uint32_t* const cbuf = wc.cbuf;
-  uint32_t* const bitmaps = wc.bitmaps;
-  uint32_t& phase_bits = wc.phase_bits;
-  uint32_t& pending = wc.pending;
-  const DeviceDfa& D = p.dfa;
-  const uint32_t dead = D.dead;  // kEmpty when the DFA has no dead state
-  const uint32_t A = D.first_accept;
+// The steps of one chunk (scan_chunk below), each a function of the chunk context and
+// the lane's row state; every step is inlined, so the state stays in registers.
+
+// What a warp knows about its chunk j: the rows it covers, the staged bytes and the
+// table; constant for the chunk once its first stages have landed.
+template <int LAYOUT, int ESIZE>
+struct ChunkCtx {
   // the row's bytes arrive in boxes of BOX bytes (32 rows x BOX per stage), swizzled in
   // 16-byte chunks by the TMA unit: chunk c of row k sits at c ^ ((k / SWZ_DIV) & SWZ_MASK)
-  constexpr uint32_t BOX = box_bytes(LAYOUT), SB = kLanes * BOX;
-  constexpr uint32_t SWZ_DIV = 128u / BOX, SWZ_MASK = BOX / 16u - 1u;
-  const uint32_t nblk = (uint32_t)(p.S / BOX);
-  const uint32_t issue_first = nblk < kStages ? nblk : kStages;
-  const uint32_t cap = p.spec_cap;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const uint64_t row0 = j * kLanes;
-  const uint64_t myrow = row0 + lane;
-  const bool active = myrow < p.R;
-  const uint32_t nrows = (uint32_t)((p.R - row0) < kLanes ? (p.R - row0) : kLanes);
-  const uint8_t* body = p.text + p.h;  // 16-byte aligned
-  const bool last_row = active && myrow == p.R - 1;
-  const uint64_t rowlen = p.S + (last_row ? p.tail : 0);
+  static constexpr uint32_t BOX = box_bytes(LAYOUT), SB = kLanes * BOX;
+  static constexpr uint32_t SWZ_DIV = 128u / BOX, SWZ_MASK = BOX / 16u - 1u;
+  WarpCtx& wc;
+  const Tab<LAYOUT, ESIZE>& tab;
+  const ScanParams& p;
+  const CUtensorMap* tmap;
+  uint64_t j;
+  uint32_t lane;
+  uint32_t dead;         // kEmpty when the DFA has no dead state
+  uint32_t A;            // first accepting state
+  uint32_t nblk;         // boxes per row
+  uint32_t issue_first;  // stages issued at the start of the chunk
+  uint32_t cap;          // speculation cap (bytes)
+  unsigned lt_mask;
+  uint64_t row0, myrow;  // first row of the chunk, the lane's row
+  bool active, last_row; // the lane has a row; it is the text's last full row
+  uint32_t nrows;        // rows of the chunk
+  const uint8_t* body;   // the text after the head (16-byte aligned)
+  uint64_t rowlen;       // the lane's row length (the last row takes the tail)
+  uint32_t staged = 0;   // bytes of every row in the first stages (set by chunk_begin)
 
-#if PAREM_PHASE_STATS
-  const uint32_t clk0 = (uint32_t)clock64();
-#endif
+  __device__ __forceinline__ ChunkCtx(WarpCtx& w, const Tab<LAYOUT, ESIZE>& t, const ScanParams& pp,
+                                      const CUtensorMap* tm, uint64_t jj)
+      : wc(w), tab(t), p(pp), tmap(tm), j(jj) {
+    lane = wc.lane;
+    dead = p.dfa.dead;
+    A = p.dfa.first_accept;
+    nblk = (uint32_t)(p.S / BOX);
+    issue_first = nblk < kStages ? nblk : kStages;
+    cap = p.spec_cap;
+    lt_mask = (1u << lane) - 1u;
+    row0 = j * kLanes;
+    myrow = row0 + lane;
+    active = myrow < p.R;
+    nrows = (uint32_t)((p.R - row0) < kLanes ? (p.R - row0) : kLanes);
+    body = p.text + p.h;
+    last_row = active && myrow == p.R - 1;
+    rowlen = p.S + (last_row ? p.tail : 0);
+  }
+  // 16 staged bytes of row k at offset pos (pos < staged)
+  __device__ __forceinline__ uint4 staged16(uint32_t k, uint32_t pos) const {
+    const uint32_t b = pos / BOX;
+    const uint32_t ch = ((pos % BOX) / 16u) ^ ((k / SWZ_DIV) & SWZ_MASK);
+    return *reinterpret_cast<const uint4*>(wc.sm + wc.stage0 + b * SB + k * BOX + ch * 16u);
+  }
+  // the class whose candidate list speculates row r: that of the byte ending row r - 1
+  __device__ __forceinline__ uint32_t cand_class(uint64_t r) const {
+    return p.enum_all ? p.dfa.n_classes : (uint32_t)p.dfa.byte_class[ldg8(body + r * p.S - 1)];
+  }
+};
+
+// The lane's row through the speculation steps.
+struct RowSpec {
+  uint32_t my_off = 0, my_m = 0;  // the row's candidate list (offset, size)
+  bool failed = false;            // a stage wait ran out (the error word is set)
+  uint32_t my_t = 0;              // offset where the candidates merged (S: never)
+  uint32_t my_sigma = kEmpty;     // the merged state at my_t
+  uint32_t my_conv = 1;           // the candidates merged
+  uint32_t head_cnt = 0;          // row 0: matches in the head bytes
+  uint32_t my_hand = 0;           // survivors handed to the lane-parallel phase
+  uint32_t my_sync = 0;           // merged at a synchronising byte
+  unsigned long long spec_lk = 0; // speculation lookups of the chunk (warp-uniform)
+};
+
+// The lane's main run: its end state, match count and the vectors holding matches.
+struct RowMain {
+  uint32_t s = 0, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0, E = 0;
+};
+
+// 1. Start the chunk's TMA pipeline, look up every row's candidate list while the first
+// stages are in flight, and wait for those stages.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void chunk_begin(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  uint8_t* const sm = C.wc.sm;
+  const uint32_t lane = C.lane;
+  const uint32_t stage0 = C.wc.stage0;
+  const uint32_t bar0 = C.wc.bar0;
+  uint32_t& phase_bits = C.wc.phase_bits;
+  uint32_t& pending = C.wc.pending;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t issue_first = C.issue_first;
+  const uint64_t row0 = C.row0;
+  const uint64_t myrow = C.myrow;
+  const bool active = C.active;
+  const ScanParams& p = C.p;
+  const CUtensorMap* const tmap = C.tmap;
+  constexpr uint32_t BOX = ChunkCtx<LAYOUT, ESIZE>::BOX;
+  constexpr uint32_t SB = ChunkCtx<LAYOUT, ESIZE>::SB;
+  auto cand_class = [&](uint64_t r) -> uint32_t { return C.cand_class(r); };
+  auto& my_off = R.my_off;
+  auto& my_m = R.my_m;
+  auto& failed = R.failed;
   // 1. start the TMA pipeline for this chunk
   if (lane == 0) {
     for (uint32_t b = 0; b < issue_first; ++b) {
@@ -461,40 +530,43 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
   }
   pending |= (1u << issue_first) - 1u;
-  auto cand_class = [&](uint64_t r) -> uint32_t {
-    return p.enum_all ? D.n_classes : (uint32_t)D.byte_class[ldg8(body + r * p.S - 1)];
-  };
   // the candidate list of every row of the chunk (row k: lane k), looked up by the lanes at
   // once while the first stages are in flight: the class of the byte that ends the previous
   // row and the bounds of its list (a chain of dependent global loads, paid once per chunk)
-  uint32_t my_off = 0, my_m = 0;
   if (active && myrow > 0) {
     const uint32_t cls = cand_class(myrow);
     my_off = D.img_off[cls];
     my_m = D.img_off[cls + 1] - my_off;
   }
-  bool failed = false;
   for (uint32_t b = 0; b < issue_first && !failed; ++b) {
     if (!stage_wait(smem_u32(sm + bar0 + 8 * b), (phase_bits >> b) & 1u, p.wait_budget, p.result)) {
       set_error(p.result, kErrTimeout);
       failed = true;
     }
   }
-  // the first bytes of every row of the chunk are already staged in shared memory
-  const uint32_t staged = issue_first * BOX;
-  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 {
-    const uint32_t b = pos / BOX;
-    const uint32_t ch = ((pos % BOX) / 16u) ^ ((k / SWZ_DIV) & SWZ_MASK);
-    return *reinterpret_cast<const uint4*>(sm + stage0 + b * SB + k * BOX + ch * 16u);
-  };
+  C.staged = issue_first * BOX;
+}
 
-  uint32_t my_t = 0, my_sigma = kEmpty, my_conv = 1, head_cnt = 0, my_hand = 0;
+// Rows merged at a synchronising byte in their staged bytes.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void find_sync_byte(const ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  uint8_t* const sm = C.wc.sm;
+  const uint32_t lane = C.lane;
+  const uint64_t myrow = C.myrow;
+  const bool active = C.active;
+  const uint32_t staged = C.staged;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 { return C.staged16(k, pos); };
+  auto& failed = R.failed;
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_sync = R.my_sync;
   // Rows that reach a synchronising byte early need no speculation: a byte whose class has
   // a one-state candidate list (Algorithm 1's R = S n L of the position after it is that
   // state for every live start) fixes the run.  Each lane looks for one in the staged bytes of
   // its row and runs that state to the next 16-byte boundary; the row is then merged at that
   // offset (the resolved start replays the bytes before it, as for any merged prefix).
-  uint32_t my_sync = 0;
   if (active && myrow > 0 && !p.enum_all && !failed && staged >= 32) {
     const uint16_t* sync = reinterpret_cast<const uint16_t*>(sm + kSyncOff);
     uint32_t t0 = kEmpty, x = 0;
@@ -522,488 +594,574 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       my_sync = 1;
     }
   }
-  // speculation work of this chunk (warp-uniform): live candidates after each merge check
-  // times the steps to the next check
-  unsigned long long spec_lk = 0;
-  if constexpr (P == 1) {
-    // 2. grouped speculation: G lanes per row, 32/G rows per pass
-    const uint32_t G = p.group;
-    const uint32_t rpp = kLanes / G;
-    const uint32_t gi = lane / G, gl = lane % G;
-    const unsigned gmask = (G == 32u) ? kFull : (((1u << G) - 1u) << (gi * G));
-    for (uint32_t k0 = 0; k0 < nrows && !failed; k0 += rpp) {
-      const uint32_t k = k0 + gi;
-      const bool valid = k < nrows;
-      const uint64_t r = row0 + k;
-      const uint32_t off = __shfl_sync(kFull, my_off, k & 31u), m = __shfl_sync(kFull, my_m, k & 31u);
-      const bool synced = __shfl_sync(kFull, my_sync, k & 31u) != 0;
-      uint32_t st = kEmpty, hc = 0;
-      bool exact = false;
-      if (valid) {
-        if (r == 0) {
-          // row 0 starts from the exact state: the initial state run over the head bytes
-          if (gl == 0) {
-            st = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &hc);
-            if (st == dead) st = kEmpty;
-          }
-          exact = true;
-        } else if (!synced) {
-          if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
+}
+
+// 2. Grouped speculation (candidate sets of at most 32 states).
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void speculate_grouped(const ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  const uint32_t lane = C.lane;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t dead = C.dead;
+  const uint32_t A = C.A;
+  const uint32_t cap = C.cap;
+  const uint64_t row0 = C.row0;
+  const uint32_t nrows = C.nrows;
+  const uint8_t* const body = C.body;
+  const uint32_t staged = C.staged;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 { return C.staged16(k, pos); };
+  auto& my_off = R.my_off;
+  auto& my_m = R.my_m;
+  auto& failed = R.failed;
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_conv = R.my_conv;
+  auto& head_cnt = R.head_cnt;
+  auto& my_sync = R.my_sync;
+  auto& spec_lk = R.spec_lk;
+  // 2. grouped speculation: G lanes per row, 32/G rows per pass
+  const uint32_t G = p.group;
+  const uint32_t rpp = kLanes / G;
+  const uint32_t gi = lane / G, gl = lane % G;
+  const unsigned gmask = (G == 32u) ? kFull : (((1u << G) - 1u) << (gi * G));
+  for (uint32_t k0 = 0; k0 < nrows && !failed; k0 += rpp) {
+    const uint32_t k = k0 + gi;
+    const bool valid = k < nrows;
+    const uint64_t r = row0 + k;
+    const uint32_t off = __shfl_sync(kFull, my_off, k & 31u), m = __shfl_sync(kFull, my_m, k & 31u);
+    const bool synced = __shfl_sync(kFull, my_sync, k & 31u) != 0;
+    uint32_t st = kEmpty, hc = 0;
+    bool exact = false;
+    if (valid) {
+      if (r == 0) {
+        // row 0 starts from the exact state: the initial state run over the head bytes
+        if (gl == 0) {
+          st = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &hc);
+          if (st == dead) st = kEmpty;
         }
-      }
-      // a row whose group has at most one live lane is already merged at t = 0
-      unsigned live = __ballot_sync(kFull, st != kEmpty);
-      bool done = exact || !valid || synced || __popc(live & gmask) <= 1;
-      uint32_t pos = 0, outcome = 1;
-      const uint8_t* grow = body + (row0 + (valid ? k : 0u)) * p.S;
-      const uint32_t kk = valid ? k : 0u;
-      RowAhead<false> ra;
-      ra.init(grow, staged, (uint32_t)p.S);
-      while (!__all_sync(kFull, done)) {
-        if (!done && pos >= cap) {
-          done = true;
-          outcome = 3;
-        }
-#if PAREM_CONV_STATS
-        spec_lk += 16u * (uint32_t)__popc(__ballot_sync(kFull, !done && st != kEmpty));
-#endif
-        const uint4 v = pos < staged ? staged16(kk, pos) : ra.get(grow, pos, (uint32_t)p.S);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-          for (int i2 = 0; i2 < 4; ++i2) {
-            if (!done && st != kEmpty) {
-              const uint32_t s2 = tab.next(st, tab.col(byte_of(v, q * 4 + i2)));
-              st = (s2 == dead) ? kEmpty : s2;
-            }
-          }
-          const uint32_t key = st == kEmpty ? kEmpty : ((gi << 16) | st);
-          const unsigned grp = __match_any_sync(kFull, key);
-          if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
-        }
-        if (!done) {
-          if (pos >= staged) ra.shift(grow, pos, (uint32_t)p.S);
-          pos += 16;
-        }
-        live = __ballot_sync(kFull, st != kEmpty);
-        if (!done && __popc(live & gmask) <= 1) done = true;
-      }
-      // the surviving state of each row (or dead) and the outcome go to the row's lane
-      live = __ballot_sync(kFull, st != kEmpty);
-      const unsigned mine = live & gmask;
-      const uint32_t sig = __shfl_sync(kFull, st, mine ? (uint32_t)(__ffs(mine) - 1) : gi * G);
-      const uint32_t sigma_row = mine ? sig : dead;
-      const uint32_t hcg = __shfl_sync(kFull, hc, gi * G);
-      // lane k (k in [k0, k0 + rpp)) collects from group k - k0
-      const uint32_t from = ((lane - k0) % rpp) * G;
-      const uint32_t o_sig = __shfl_sync(kFull, sigma_row, from);
-      const uint32_t o_out = __shfl_sync(kFull, outcome, from);
-      const uint32_t o_pos = __shfl_sync(kFull, pos, from);
-      const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
-      if (lane >= k0 && lane < k0 + rpp && lane < nrows && !my_sync) {
-        my_conv = o_out == 1;
-        my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
-        my_sigma = o_out == 1 ? o_sig : kEmpty;
-        head_cnt = o_hc;
+        exact = true;
+      } else if (!synced) {
+        if (gl < m && m <= G) st = (uint32_t)D.img[off + gl];
       }
     }
-    if (row0 != 0 || lane != 0) head_cnt = 0;
-  } else {
-    // 2a. warp-wide speculation, one row at a time, candidates across lanes and registers
-    for (uint32_t k = 0; k < nrows && !failed; ++k) {
-      const uint64_t r = row0 + k;
-      if (r == 0) {
-        uint32_t c0 = 0;
-        const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
-        if (lane == 0) {
-          my_t = 0;
-          my_sigma = sh;
-          head_cnt = c0;
-        }
-        continue;
+    // a row whose group has at most one live lane is already merged at t = 0
+    unsigned live = __ballot_sync(kFull, st != kEmpty);
+    bool done = exact || !valid || synced || __popc(live & gmask) <= 1;
+    uint32_t pos = 0, outcome = 1;
+    const uint8_t* grow = body + (row0 + (valid ? k : 0u)) * p.S;
+    const uint32_t kk = valid ? k : 0u;
+    RowAhead<false> ra;
+    ra.init(grow, staged, (uint32_t)p.S);
+    while (!__all_sync(kFull, done)) {
+      if (!done && pos >= cap) {
+        done = true;
+        outcome = 3;
       }
-      if (__shfl_sync(kFull, my_sync, k)) continue;  // merged at a synchronising byte
-      const uint32_t off = __shfl_sync(kFull, my_off, k), m = __shfl_sync(kFull, my_m, k);
-      const bool big = m > 32u * P;
-      if (m <= 1 || (big && p.bitmap_words == 0)) {
-        if (lane == k) {
-          my_t = big ? (uint32_t)p.S : 0u;
-          my_conv = m <= 1;
-          my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
-        }
-        continue;
-      }
-      uint32_t st[P];
-      uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
-      uint32_t live_n = m;  // live candidates after the last merge check (warp-uniform)
-      uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
-#if PAREM_PHASE_STATS
-      const uint32_t cb0 = (uint32_t)clock64();
-#endif
-      if (big) {
-        // More candidates than registers: the warp keeps the candidate set as a bitmap over
-        // the states (duplicates merge by construction) until it fits 32 * P registers.
-        const uint32_t W = p.bitmap_words;
-        uint32_t* bm0 = bitmaps;
-        uint32_t* bm1 = bitmaps + W;
-        for (uint32_t w = lane; w < W; w += 32) bm0[w] = 0;
-        __syncwarp();
-        for (uint32_t slot = lane; slot < m; slot += 32) {
-          const uint32_t q = D.img[off + slot];
-          atomicOr(&bm0[q >> 5], 1u << (q & 31u));
-        }
-        __syncwarp();
-        uint32_t cnt = m;
-        const uint8_t* brow = body + r * p.S;
-        RowAhead<(P >= 4)> ra;
-        ra.init(brow, pos > staged ? pos : staged, (uint32_t)p.S);
-        for (;;) {
-          if (pos >= cap) {
-            outcome = 3;
-            break;
-          }
-          const uint4 v = pos < staged ? staged16(k, pos) : ra.get(brow, pos, (uint32_t)p.S);
-          if (pos >= staged) ra.shift(brow, pos, (uint32_t)p.S);
 #if PAREM_CONV_STATS
-          spec_lk += 16u * live_n;
+      spec_lk += 16u * (uint32_t)__popc(__ballot_sync(kFull, !done && st != kEmpty));
 #endif
-#pragma unroll 1
-          for (int q = 0; q < 16; ++q) {
-            const uint32_t c = tab.col(byte_of(v, q));
-            for (uint32_t w = lane; w < W; w += 32) bm1[w] = 0;
-            __syncwarp();
-            for (uint32_t w = lane; w < W; w += 32) {
-              uint32_t bits = bm0[w];
-              while (bits) {
-                // up to four independent lookups in flight
-                uint32_t qs[4], nq[4];
+      const uint4 v = pos < staged ? staged16(kk, pos) : ra.get(grow, pos, (uint32_t)p.S);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  qs[u] = kEmpty;
-                  if (bits) {
-                    qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
-                    bits &= bits - 1;
-                  }
-                }
+      for (int q = 0; q < 4; ++q) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) nq[u] = qs[u] != kEmpty ? tab.next(qs[u], c) : dead;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
-              }
-            }
-            __syncwarp();
-            uint32_t* tmp = bm0;
-            bm0 = bm1;
-            bm1 = tmp;
+        for (int i2 = 0; i2 < 4; ++i2) {
+          if (!done && st != kEmpty) {
+            const uint32_t s2 = tab.next(st, tab.col(byte_of(v, q * 4 + i2)));
+            st = (s2 == dead) ? kEmpty : s2;
           }
-          pos += 16;
-          uint32_t local = 0;
-          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
-          cnt = __reduce_add_sync(kFull, local);
-          live_n = cnt;
-          if (cnt <= 32u * P) break;
         }
-#if PAREM_PHASE_STATS
-        if (lane == 0) wc.cyc[3] += (uint32_t)clock64() - cb0;
-#endif
-        if (outcome == 0) {
-          // list the surviving states in the hand-over buffer, then load the registers
-          uint32_t local = 0;
-          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
-          uint32_t incl = local;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(kFull, incl, d);
-            if (lane >= (uint32_t)d) incl += o;
-          }
-          uint32_t idx = incl - local;
-          // the list has its own buffer after the two bitmaps: the hand-over lists of
-          // earlier rows of this chunk must survive until phase 2b
-          uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
-          for (uint32_t w = lane; w < W; w += 32) {
-            uint32_t bits = bm0[w];
-            while (bits) {
-              list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
-              bits &= bits - 1;
-            }
-          }
-          __syncwarp();
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const uint32_t slot = (uint32_t)i * 32u + lane;
-            st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
-            if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
-          }
-          __syncwarp();
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          const uint32_t slot = (uint32_t)i * 32u + lane;
-          st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
-          if ((uint32_t)i * 32u < m) lr |= 1u << i;
-        }
+        const uint32_t key = st == kEmpty ? kEmpty : ((gi << 16) | st);
+        const unsigned grp = __match_any_sync(kFull, key);
+        if (st != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st = kEmpty;
       }
-      const uint8_t* wrow = body + r * p.S;
-      RowAhead<(P >= 4)> wa;
-      wa.init(wrow, pos > staged ? pos : staged, (uint32_t)p.S);
-      for (; outcome == 0;) {
+      if (!done) {
+        if (pos >= staged) ra.shift(grow, pos, (uint32_t)p.S);
+        pos += 16;
+      }
+      live = __ballot_sync(kFull, st != kEmpty);
+      if (!done && __popc(live & gmask) <= 1) done = true;
+    }
+    // the surviving state of each row (or dead) and the outcome go to the row's lane
+    live = __ballot_sync(kFull, st != kEmpty);
+    const unsigned mine = live & gmask;
+    const uint32_t sig = __shfl_sync(kFull, st, mine ? (uint32_t)(__ffs(mine) - 1) : gi * G);
+    const uint32_t sigma_row = mine ? sig : dead;
+    const uint32_t hcg = __shfl_sync(kFull, hc, gi * G);
+    // lane k (k in [k0, k0 + rpp)) collects from group k - k0
+    const uint32_t from = ((lane - k0) % rpp) * G;
+    const uint32_t o_sig = __shfl_sync(kFull, sigma_row, from);
+    const uint32_t o_out = __shfl_sync(kFull, outcome, from);
+    const uint32_t o_pos = __shfl_sync(kFull, pos, from);
+    const uint32_t o_hc = __shfl_sync(kFull, hcg, from);
+    if (lane >= k0 && lane < k0 + rpp && lane < nrows && !my_sync) {
+      my_conv = o_out == 1;
+      my_t = o_out == 3 ? (uint32_t)p.S : o_pos;
+      my_sigma = o_out == 1 ? o_sig : kEmpty;
+      head_cnt = o_hc;
+    }
+  }
+  if (row0 != 0 || lane != 0) head_cnt = 0;
+}
+
+// 2a. Warp-wide speculation over P registers per lane.
+template <int LAYOUT, int ESIZE, int P>
+__device__ __forceinline__ void speculate_warp(const ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  const uint32_t lane = C.lane;
+  uint16_t* const hand = C.wc.hand;
+  uint32_t* const cbuf = C.wc.cbuf;
+  uint32_t* const bitmaps = C.wc.bitmaps;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t dead = C.dead;
+  const uint32_t A = C.A;
+  const uint32_t cap = C.cap;
+  const unsigned lt_mask = C.lt_mask;
+  const uint64_t row0 = C.row0;
+  const uint32_t nrows = C.nrows;
+  const uint8_t* const body = C.body;
+  const uint32_t staged = C.staged;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  WarpCtx& wc = C.wc;
+  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 { return C.staged16(k, pos); };
+  auto& my_off = R.my_off;
+  auto& my_m = R.my_m;
+  auto& failed = R.failed;
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_conv = R.my_conv;
+  auto& head_cnt = R.head_cnt;
+  auto& my_hand = R.my_hand;
+  auto& my_sync = R.my_sync;
+  auto& spec_lk = R.spec_lk;
+  // 2a. warp-wide speculation, one row at a time, candidates across lanes and registers
+  for (uint32_t k = 0; k < nrows && !failed; ++k) {
+    const uint64_t r = row0 + k;
+    if (r == 0) {
+      uint32_t c0 = 0;
+      const uint32_t sh = run_bytes(tab, p.text, p.h, p.init_state, dead, A, &c0);
+      if (lane == 0) {
+        my_t = 0;
+        my_sigma = sh;
+        head_cnt = c0;
+      }
+      continue;
+    }
+    if (__shfl_sync(kFull, my_sync, k)) continue;  // merged at a synchronising byte
+    const uint32_t off = __shfl_sync(kFull, my_off, k), m = __shfl_sync(kFull, my_m, k);
+    const bool big = m > 32u * P;
+    if (m <= 1 || (big && p.bitmap_words == 0)) {
+      if (lane == k) {
+        my_t = big ? (uint32_t)p.S : 0u;
+        my_conv = m <= 1;
+        my_sigma = m == 1 ? (uint32_t)D.img[off] : dead;
+      }
+      continue;
+    }
+    uint32_t st[P];
+    uint32_t lr = 0;  // registers that may hold live candidates (warp-uniform)
+    uint32_t live_n = m;  // live candidates after the last merge check (warp-uniform)
+    uint32_t pos = 0, sigma = kEmpty, outcome = 0;  // 1 merged, 2 handed to the lane, 3 not merging
+#if PAREM_PHASE_STATS
+    const uint32_t cb0 = (uint32_t)clock64();
+#endif
+    if (big) {
+      // More candidates than registers: the warp keeps the candidate set as a bitmap over
+      // the states (duplicates merge by construction) until it fits 32 * P registers.
+      const uint32_t W = p.bitmap_words;
+      uint32_t* bm0 = bitmaps;
+      uint32_t* bm1 = bitmaps + W;
+      for (uint32_t w = lane; w < W; w += 32) bm0[w] = 0;
+      __syncwarp();
+      for (uint32_t slot = lane; slot < m; slot += 32) {
+        const uint32_t q = D.img[off + slot];
+        atomicOr(&bm0[q >> 5], 1u << (q & 31u));
+      }
+      __syncwarp();
+      uint32_t cnt = m;
+      const uint8_t* brow = body + r * p.S;
+      RowAhead<(P >= 4)> ra;
+      ra.init(brow, pos > staged ? pos : staged, (uint32_t)p.S);
+      for (;;) {
         if (pos >= cap) {
           outcome = 3;
           break;
         }
-        const uint4 v = pos < staged ? staged16(k, pos) : wa.get(wrow, pos, (uint32_t)p.S);
-        if (pos >= staged) wa.shift(wrow, pos, (uint32_t)p.S);
+        const uint4 v = pos < staged ? staged16(k, pos) : ra.get(brow, pos, (uint32_t)p.S);
+        if (pos >= staged) ra.shift(brow, pos, (uint32_t)p.S);
 #if PAREM_CONV_STATS
         spec_lk += 16u * live_n;
 #endif
-        if (p.bitmap_words) {
-          // 16 steps with no merging inside them, then one merge of equal states across all
-          // lanes and registers through the state bitmap, which also packs the survivors
-          // densely into the first registers
-#pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const uint32_t c = tab.col(byte_of(v, q));
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              if ((lr >> i) & 1u) {
-                if (st[i] != kEmpty) {
-                  const uint32_t s2 = tab.next(st[i], c);
-                  st[i] = (s2 == dead) ? kEmpty : s2;
-                }
-              }
-            }
-          }
-          pos += 16;
-          const uint32_t W = p.bitmap_words;
-          uint32_t* bm = bitmaps;
-          for (uint32_t w = lane; w < W; w += 32) bm[w] = 0;
+#pragma unroll 1
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t c = tab.col(byte_of(v, q));
+          for (uint32_t w = lane; w < W; w += 32) bm1[w] = 0;
           __syncwarp();
-#pragma unroll
-          for (int i = 0; i < P; ++i)
-            if (((lr >> i) & 1u) && st[i] != kEmpty) atomicOr(&bm[st[i] >> 5], 1u << (st[i] & 31u));
-          __syncwarp();
-          uint32_t local = 0;
-          for (uint32_t w = lane; w < W; w += 32) local += __popc(bm[w]);
-          uint32_t incl = local;
-#pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t o = __shfl_up_sync(kFull, incl, d);
-            if (lane >= (uint32_t)d) incl += o;
-          }
-          const uint32_t cnt = __shfl_sync(kFull, incl, 31);
-          live_n = cnt;
-          uint32_t idx = incl - local;
-          uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
           for (uint32_t w = lane; w < W; w += 32) {
-            uint32_t bits = bm[w];
+            uint32_t bits = bm0[w];
             while (bits) {
-              list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
-              bits &= bits - 1;
-            }
-          }
-          __syncwarp();
-          lr = 0;
+              // up to four independent lookups in flight
+              uint32_t qs[4], nq[4];
 #pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const uint32_t slot = (uint32_t)i * 32u + lane;
-            st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
-            if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
-          }
-          __syncwarp();
-          if (cnt <= 1) {
-            outcome = 1;
-            sigma = cnt ? __shfl_sync(kFull, st[0], 0) : dead;
-            break;
-          }
-          if (cnt <= kLaneCand) {
-            // few survivors left: the lane that owns the row finishes them (phase 2b)
-            if (lane < cnt) hand[k * kLaneCand + lane] = (uint16_t)st[0];
-            sigma = cnt;
-            outcome = 2;
-            break;
-          }
-          continue;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-#pragma unroll
-          for (int i2 = 0; i2 < 4; ++i2) {
-            const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
-#pragma unroll
-            for (int i = 0; i < P; ++i) {
-              if ((lr >> i) & 1u) {
-                if (st[i] != kEmpty) {
-                  const uint32_t s2 = tab.next(st[i], c);
-                  st[i] = (s2 == dead) ? kEmpty : s2;
+              for (int u = 0; u < 4; ++u) {
+                qs[u] = kEmpty;
+                if (bits) {
+                  qs[u] = w * 32u + (uint32_t)(__ffs(bits) - 1);
+                  bits &= bits - 1;
                 }
               }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) nq[u] = qs[u] != kEmpty ? tab.next(qs[u], c) : dead;
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (qs[u] != kEmpty && nq[u] != dead) atomicOr(&bm1[nq[u] >> 5], 1u << (nq[u] & 31u));
             }
           }
-          // merge lanes whose candidates met (within each register)
+          __syncwarp();
+          uint32_t* tmp = bm0;
+          bm0 = bm1;
+          bm1 = tmp;
+        }
+        pos += 16;
+        uint32_t local = 0;
+        for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+        cnt = __reduce_add_sync(kFull, local);
+        live_n = cnt;
+        if (cnt <= 32u * P) break;
+      }
+#if PAREM_PHASE_STATS
+      if (lane == 0) wc.cyc[3] += (uint32_t)clock64() - cb0;
+#endif
+      if (outcome == 0) {
+        // list the surviving states in the hand-over buffer, then load the registers
+        uint32_t local = 0;
+        for (uint32_t w = lane; w < W; w += 32) local += __popc(bm0[w]);
+        uint32_t incl = local;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t o = __shfl_up_sync(kFull, incl, d);
+          if (lane >= (uint32_t)d) incl += o;
+        }
+        uint32_t idx = incl - local;
+        // the list has its own buffer after the two bitmaps: the hand-over lists of
+        // earlier rows of this chunk must survive until phase 2b
+        uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
+        for (uint32_t w = lane; w < W; w += 32) {
+          uint32_t bits = bm0[w];
+          while (bits) {
+            list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
+            bits &= bits - 1;
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          const uint32_t slot = (uint32_t)i * 32u + lane;
+          st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
+          if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
+        }
+        __syncwarp();
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const uint32_t slot = (uint32_t)i * 32u + lane;
+        st[i] = slot < m ? (uint32_t)D.img[off + slot] : kEmpty;
+        if ((uint32_t)i * 32u < m) lr |= 1u << i;
+      }
+    }
+    const uint8_t* wrow = body + r * p.S;
+    RowAhead<(P >= 4)> wa;
+    wa.init(wrow, pos > staged ? pos : staged, (uint32_t)p.S);
+    for (; outcome == 0;) {
+      if (pos >= cap) {
+        outcome = 3;
+        break;
+      }
+      const uint4 v = pos < staged ? staged16(k, pos) : wa.get(wrow, pos, (uint32_t)p.S);
+      if (pos >= staged) wa.shift(wrow, pos, (uint32_t)p.S);
+#if PAREM_CONV_STATS
+      spec_lk += 16u * live_n;
+#endif
+      if (p.bitmap_words) {
+        // 16 steps with no merging inside them, then one merge of equal states across all
+        // lanes and registers through the state bitmap, which also packs the survivors
+        // densely into the first registers
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t c = tab.col(byte_of(v, q));
 #pragma unroll
           for (int i = 0; i < P; ++i) {
             if ((lr >> i) & 1u) {
-              const unsigned grp = __match_any_sync(kFull, st[i]);
-              if (st[i] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[i] = kEmpty;
+              if (st[i] != kEmpty) {
+                const uint32_t s2 = tab.next(st[i], c);
+                st[i] = (s2 == dead) ? kEmpty : s2;
+              }
             }
           }
         }
         pos += 16;
-        uint32_t total = 0, nlr = 0;
-        unsigned bl[P];
+        const uint32_t W = p.bitmap_words;
+        uint32_t* bm = bitmaps;
+        for (uint32_t w = lane; w < W; w += 32) bm[w] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+          if (((lr >> i) & 1u) && st[i] != kEmpty) atomicOr(&bm[st[i] >> 5], 1u << (st[i] & 31u));
+        __syncwarp();
+        uint32_t local = 0;
+        for (uint32_t w = lane; w < W; w += 32) local += __popc(bm[w]);
+        uint32_t incl = local;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t o = __shfl_up_sync(kFull, incl, d);
+          if (lane >= (uint32_t)d) incl += o;
+        }
+        const uint32_t cnt = __shfl_sync(kFull, incl, 31);
+        live_n = cnt;
+        uint32_t idx = incl - local;
+        uint16_t* list = reinterpret_cast<uint16_t*>(bitmaps + 2 * W);
+        for (uint32_t w = lane; w < W; w += 32) {
+          uint32_t bits = bm[w];
+          while (bits) {
+            list[idx++] = (uint16_t)(w * 32u + (uint32_t)(__ffs(bits) - 1));
+            bits &= bits - 1;
+          }
+        }
+        __syncwarp();
+        lr = 0;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
-          bl[i] = ((lr >> i) & 1u) ? __ballot_sync(kFull, st[i] != kEmpty) : 0u;
-          total += __popc(bl[i]);
-          if (bl[i]) nlr |= 1u << i;
+          const uint32_t slot = (uint32_t)i * 32u + lane;
+          st[i] = slot < cnt ? (uint32_t)list[slot] : kEmpty;
+          if ((uint32_t)i * 32u < cnt) lr |= 1u << i;
         }
-        lr = nlr;
-        if (total <= 32 && (lr & ~1u)) {
-          // all survivors fit one register: compact them into register 0, then merge
-          uint32_t base = 0;
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            if (st[i] != kEmpty) cbuf[base + __popc(bl[i] & lt_mask)] = st[i];
-            base += __popc(bl[i]);
-          }
-          __syncwarp();
-          st[0] = lane < total ? cbuf[lane] : kEmpty;
-#pragma unroll
-          for (int i = 1; i < P; ++i) st[i] = kEmpty;
-          __syncwarp();
-          const unsigned grp = __match_any_sync(kFull, st[0]);
-          if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
-          bl[0] = __ballot_sync(kFull, st[0] != kEmpty);
-#pragma unroll
-          for (int i = 1; i < P; ++i) bl[i] = 0;
-          total = __popc(bl[0]);
-          lr = 1;
-        }
-        live_n = total;
-        if (total <= 1) {
+        __syncwarp();
+        if (cnt <= 1) {
           outcome = 1;
-          if (total == 0) {
-            sigma = dead;
-          } else {
-            uint32_t reg = 0, holder = 0;
-#pragma unroll
-            for (int i = P - 1; i >= 0; --i)
-              if (bl[i]) {
-                reg = (uint32_t)i;
-                holder = __ffs(bl[i]) - 1;
-              }
-            uint32_t val = kEmpty;
-#pragma unroll
-            for (int i = 0; i < P; ++i)
-              if ((uint32_t)i == reg) val = st[i];
-            sigma = __shfl_sync(kFull, val, holder);
-          }
+          sigma = cnt ? __shfl_sync(kFull, st[0], 0) : dead;
           break;
         }
-        if (total <= kLaneCand && lr == 1u) {
+        if (cnt <= kLaneCand) {
           // few survivors left: the lane that owns the row finishes them (phase 2b)
-          if (st[0] != kEmpty) hand[k * kLaneCand + __popc(bl[0] & lt_mask)] = (uint16_t)st[0];
-          sigma = total;
+          if (lane < cnt) hand[k * kLaneCand + lane] = (uint16_t)st[0];
+          sigma = cnt;
           outcome = 2;
           break;
         }
+        continue;
       }
-      if (lane == k) {
-        my_conv = outcome == 1;
-        my_t = outcome == 3 ? (uint32_t)p.S : pos;
-        my_sigma = outcome == 1 ? sigma : kEmpty;
-        my_hand = outcome == 2 ? sigma : 0u;
-      }
-    }
-
-#if PAREM_PHASE_STATS
-    const uint32_t cl0 = (uint32_t)clock64();
-#endif
-    // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
-    if (__ballot_sync(kFull, my_hand != 0) && !failed) {
-      __syncwarp();
-      // every lane runs the loop (lanes without survivors idle through it); the survivor
-      // slots it touches are bounded by the warp's largest survivor count, which is uniform,
-      // so slots nobody uses cost nothing
-      {
-        uint32_t ls[kLaneCand];
 #pragma unroll
-        for (uint32_t i = 0; i < kLaneCand; ++i)
-          ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
-        uint32_t L = my_hand, pos = my_t, lk2 = 0;
-        bool busy = my_hand != 0;
-        const uint8_t* lrow = body + (active ? myrow : row0) * p.S;
-        RowAhead<(P >= 4)> la;
-        if (busy) la.init(lrow, pos > staged ? pos : staged, (uint32_t)p.S);
-        for (;;) {
-          if (busy && pos >= cap) {
-            my_conv = 0;
-            my_t = (uint32_t)p.S;
-            busy = false;
-          }
-          const uint32_t lmax = __reduce_max_sync(kFull, busy ? L : 0u);
-          if (lmax == 0) break;
-          lk2 += busy ? 16u * L : 0u;
-          const uint4 v = !busy ? make_uint4(0, 0, 0, 0) : pos < staged ? staged16(lane, pos) : la.get(lrow, pos, (uint32_t)p.S);
-          if (busy && pos >= staged) la.shift(lrow, pos, (uint32_t)p.S);
+      for (int q = 0; q < 4; ++q) {
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const uint32_t c = tab.col(byte_of(v, q));
+        for (int i2 = 0; i2 < 4; ++i2) {
+          const uint32_t c = tab.col(byte_of(v, q * 4 + i2));
 #pragma unroll
-            for (uint32_t i = 0; i < kLaneCand; ++i) {
-              if (i < lmax) {  // warp-uniform
-                if (ls[i] != kEmpty) {
-                  const uint32_t s2 = tab.next(ls[i], c);
-                  ls[i] = (s2 == dead) ? kEmpty : s2;
-                }
+          for (int i = 0; i < P; ++i) {
+            if ((lr >> i) & 1u) {
+              if (st[i] != kEmpty) {
+                const uint32_t s2 = tab.next(st[i], c);
+                st[i] = (s2 == dead) ? kEmpty : s2;
               }
             }
           }
-          pos += 16;
-          // merge equal survivors and compact them to the front
-          uint32_t out[kLaneCand];
+        }
+        // merge lanes whose candidates met (within each register)
 #pragma unroll
-          for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
-          uint32_t np = 0;
+        for (int i = 0; i < P; ++i) {
+          if ((lr >> i) & 1u) {
+            const unsigned grp = __match_any_sync(kFull, st[i]);
+            if (st[i] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[i] = kEmpty;
+          }
+        }
+      }
+      pos += 16;
+      uint32_t total = 0, nlr = 0;
+      unsigned bl[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        bl[i] = ((lr >> i) & 1u) ? __ballot_sync(kFull, st[i] != kEmpty) : 0u;
+        total += __popc(bl[i]);
+        if (bl[i]) nlr |= 1u << i;
+      }
+      lr = nlr;
+      if (total <= 32 && (lr & ~1u)) {
+        // all survivors fit one register: compact them into register 0, then merge
+        uint32_t base = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          if (st[i] != kEmpty) cbuf[base + __popc(bl[i] & lt_mask)] = st[i];
+          base += __popc(bl[i]);
+        }
+        __syncwarp();
+        st[0] = lane < total ? cbuf[lane] : kEmpty;
+#pragma unroll
+        for (int i = 1; i < P; ++i) st[i] = kEmpty;
+        __syncwarp();
+        const unsigned grp = __match_any_sync(kFull, st[0]);
+        if (st[0] != kEmpty && (uint32_t)(__ffs(grp) - 1) != lane) st[0] = kEmpty;
+        bl[0] = __ballot_sync(kFull, st[0] != kEmpty);
+#pragma unroll
+        for (int i = 1; i < P; ++i) bl[i] = 0;
+        total = __popc(bl[0]);
+        lr = 1;
+      }
+      live_n = total;
+      if (total <= 1) {
+        outcome = 1;
+        if (total == 0) {
+          sigma = dead;
+        } else {
+          uint32_t reg = 0, holder = 0;
+#pragma unroll
+          for (int i = P - 1; i >= 0; --i)
+            if (bl[i]) {
+              reg = (uint32_t)i;
+              holder = __ffs(bl[i]) - 1;
+            }
+          uint32_t val = kEmpty;
+#pragma unroll
+          for (int i = 0; i < P; ++i)
+            if ((uint32_t)i == reg) val = st[i];
+          sigma = __shfl_sync(kFull, val, holder);
+        }
+        break;
+      }
+      if (total <= kLaneCand && lr == 1u) {
+        // few survivors left: the lane that owns the row finishes them (phase 2b)
+        if (st[0] != kEmpty) hand[k * kLaneCand + __popc(bl[0] & lt_mask)] = (uint16_t)st[0];
+        sigma = total;
+        outcome = 2;
+        break;
+      }
+    }
+    if (lane == k) {
+      my_conv = outcome == 1;
+      my_t = outcome == 3 ? (uint32_t)p.S : pos;
+      my_sigma = outcome == 1 ? sigma : kEmpty;
+      my_hand = outcome == 2 ? sigma : 0u;
+    }
+  }
+
+}
+
+// 2b. Lane-parallel speculation of the survivors the warp-wide phase handed over.
+template <int LAYOUT, int ESIZE, int P>
+__device__ __forceinline__ void speculate_lanes(const ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  const uint32_t lane = C.lane;
+  uint16_t* const hand = C.wc.hand;
+  const uint32_t dead = C.dead;
+  const uint32_t cap = C.cap;
+  const uint64_t row0 = C.row0;
+  const uint64_t myrow = C.myrow;
+  const bool active = C.active;
+  const uint8_t* const body = C.body;
+  const uint32_t staged = C.staged;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  WarpCtx& wc = C.wc;
+  auto staged16 = [&](uint32_t k, uint32_t pos) -> uint4 { return C.staged16(k, pos); };
+  auto& failed = R.failed;
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_conv = R.my_conv;
+  auto& my_hand = R.my_hand;
+  auto& spec_lk = R.spec_lk;
+#if PAREM_PHASE_STATS
+  const uint32_t cl0 = (uint32_t)clock64();
+#endif
+  // 2b. lane-parallel speculation: each lane runs the few survivors of its own row
+  if (__ballot_sync(kFull, my_hand != 0) && !failed) {
+    __syncwarp();
+    // every lane runs the loop (lanes without survivors idle through it); the survivor
+    // slots it touches are bounded by the warp's largest survivor count, which is uniform,
+    // so slots nobody uses cost nothing
+    {
+      uint32_t ls[kLaneCand];
+#pragma unroll
+      for (uint32_t i = 0; i < kLaneCand; ++i)
+        ls[i] = i < my_hand ? (uint32_t)hand[lane * kLaneCand + i] : kEmpty;
+      uint32_t L = my_hand, pos = my_t, lk2 = 0;
+      bool busy = my_hand != 0;
+      const uint8_t* lrow = body + (active ? myrow : row0) * p.S;
+      RowAhead<(P >= 4)> la;
+      if (busy) la.init(lrow, pos > staged ? pos : staged, (uint32_t)p.S);
+      for (;;) {
+        if (busy && pos >= cap) {
+          my_conv = 0;
+          my_t = (uint32_t)p.S;
+          busy = false;
+        }
+        const uint32_t lmax = __reduce_max_sync(kFull, busy ? L : 0u);
+        if (lmax == 0) break;
+        lk2 += busy ? 16u * L : 0u;
+        const uint4 v = !busy ? make_uint4(0, 0, 0, 0) : pos < staged ? staged16(lane, pos) : la.get(lrow, pos, (uint32_t)p.S);
+        if (busy && pos >= staged) la.shift(lrow, pos, (uint32_t)p.S);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const uint32_t c = tab.col(byte_of(v, q));
 #pragma unroll
           for (uint32_t i = 0; i < kLaneCand; ++i) {
-            if (i < lmax) {
-              bool keep = ls[i] != kEmpty;
-#pragma unroll
-              for (uint32_t jj = 0; jj < i; ++jj)
-                if (ls[jj] == ls[i]) keep = false;
-#pragma unroll
-              for (uint32_t qq = 0; qq < kLaneCand; ++qq)
-                if (qq <= i && keep && qq == np) out[qq] = ls[i];
-              np += keep ? 1u : 0u;
-            }
-          }
-#pragma unroll
-          for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
-          if (busy) {
-            L = np;
-            if (L <= 1) {
-              my_conv = 1;
-              my_t = pos;
-              my_sigma = L ? ls[0] : dead;
-              busy = false;
+            if (i < lmax) {  // warp-uniform
+              if (ls[i] != kEmpty) {
+                const uint32_t s2 = tab.next(ls[i], c);
+                ls[i] = (s2 == dead) ? kEmpty : s2;
+              }
             }
           }
         }
-        my_hand = 0;
-#if PAREM_CONV_STATS
-        spec_lk += __reduce_add_sync(kFull, lk2);
-#endif
+        pos += 16;
+        // merge equal survivors and compact them to the front
+        uint32_t out[kLaneCand];
+#pragma unroll
+        for (uint32_t i = 0; i < kLaneCand; ++i) out[i] = kEmpty;
+        uint32_t np = 0;
+#pragma unroll
+        for (uint32_t i = 0; i < kLaneCand; ++i) {
+          if (i < lmax) {
+            bool keep = ls[i] != kEmpty;
+#pragma unroll
+            for (uint32_t jj = 0; jj < i; ++jj)
+              if (ls[jj] == ls[i]) keep = false;
+#pragma unroll
+            for (uint32_t qq = 0; qq < kLaneCand; ++qq)
+              if (qq <= i && keep && qq == np) out[qq] = ls[i];
+            np += keep ? 1u : 0u;
+          }
+        }
+#pragma unroll
+        for (uint32_t i = 0; i < kLaneCand; ++i) ls[i] = out[i];
+        if (busy) {
+          L = np;
+          if (L <= 1) {
+            my_conv = 1;
+            my_t = pos;
+            my_sigma = L ? ls[0] : dead;
+            busy = false;
+          }
+        }
       }
-      __syncwarp();
-    }
-#if PAREM_PHASE_STATS
-    if (lane == 0) wc.cyc[4] += (uint32_t)clock64() - cl0;
+      my_hand = 0;
+#if PAREM_CONV_STATS
+      spec_lk += __reduce_add_sync(kFull, lk2);
 #endif
+    }
+    __syncwarp();
   }
+#if PAREM_PHASE_STATS
+  if (lane == 0) wc.cyc[4] += (uint32_t)clock64() - cl0;
+#endif
+}
 
+// Convergence counters of the chunk for the planner.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void record_convergence(const ChunkCtx<LAYOUT, ESIZE>& C, const RowSpec& R) {
+  const uint32_t lane = C.lane;
+  const bool active = C.active;
+  const ScanParams& p = C.p;
+  auto& my_t = R.my_t;
+  auto& my_conv = R.my_conv;
+  auto& spec_lk = R.spec_lk;
 #if PAREM_CONV_STATS
   // convergence statistics for the planner (one update per chunk)
   {
@@ -1018,7 +1176,23 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
   }
 #endif
+}
 
+// 3. Slot maps of the rows that did not merge.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ void run_slot_maps(const ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R) {
+  const uint32_t lane = C.lane;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t dead = C.dead;
+  const uint32_t A = C.A;
+  const uint64_t row0 = C.row0;
+  const bool active = C.active;
+  const uint8_t* const body = C.body;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  auto cand_class = [&](uint64_t r) -> uint32_t { return C.cand_class(r); };
+  auto& failed = R.failed;
+  auto& my_conv = R.my_conv;
   // 3. slot maps of rows whose candidates did not merge (rare): every candidate runs
   //    the whole row (and the tail on the last row), lanes over candidates
   unsigned nonconv = p.serial_fallback ? 0u : __ballot_sync(kFull, active && !my_conv);
@@ -1046,13 +1220,49 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       atomicAdd(&p.result->spec_lookups, (unsigned long long)m * (p.S + (r == p.R - 1 ? p.tail : 0)));
 #endif
   }
+}
 
-#if PAREM_PHASE_STATS
-  const uint32_t clk1 = (uint32_t)clock64();
-#endif
+// 4. The main run of every merged row (and the tail on the last row); false when a stage
+// wait ran out.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R, RowMain& M) {
+  uint8_t* const sm = C.wc.sm;
+  const uint32_t lane = C.lane;
+  const uint32_t stage0 = C.wc.stage0;
+  const uint32_t bar0 = C.wc.bar0;
+  uint32_t& phase_bits = C.wc.phase_bits;
+  uint32_t& pending = C.wc.pending;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t A = C.A;
+  const uint32_t nblk = C.nblk;
+  const uint64_t row0 = C.row0;
+  const uint64_t myrow = C.myrow;
+  const bool active = C.active;
+  const uint8_t* const body = C.body;
+  const bool last_row = C.last_row;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  const CUtensorMap* const tmap = C.tmap;
+  constexpr uint32_t BOX = ChunkCtx<LAYOUT, ESIZE>::BOX;
+  constexpr uint32_t SB = ChunkCtx<LAYOUT, ESIZE>::SB;
+  constexpr uint32_t SWZ_DIV = ChunkCtx<LAYOUT, ESIZE>::SWZ_DIV;
+  constexpr uint32_t SWZ_MASK = ChunkCtx<LAYOUT, ESIZE>::SWZ_MASK;
+  auto& failed = R.failed;
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_conv = R.my_conv;
+  auto& s = M.s;
+  auto& mu = M.mu;
+  auto& fv = M.fv;
+  auto& fs = M.fs;
+  auto& lvv = M.lvv;
+  auto& ls = M.ls;
+  auto& lv = M.lv;
+  auto& nrec = M.nrec;
+  auto& E = M.E;
   // 4. main run: each lane runs its merged state over the rest of its row from smem,
   //    remembering the first and last 16-byte vectors that contain matches
-  uint32_t s = my_sigma, mu = 0, fv = kEmpty, fs = 0, lvv = 0, ls = 0, lv = 0, nrec = 0;
+  s = my_sigma;
   const bool run = active && my_conv;
   uint32_t* myslots = p.slots ? p.slots + myrow * kRowSlots : nullptr;
   for (uint32_t blk = 0; blk < nblk && !failed; ++blk) {
@@ -1224,7 +1434,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
   }
-  if (failed) return;
+  if (failed) return false;
   lv = (fv == kEmpty) ? 0u : lvv + 16u;
   if (run && last_row && p.tail) {
     // the tail after the last full row (16-byte aligned, shorter than a row) is on the critical
@@ -1272,11 +1482,41 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
         reinterpret_cast<uint16_t*>(p.match_bits)[(p.R * p.S + o) / 16] = (uint16_t)tbits;
     }
   }
-  const uint32_t E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
+  E = s;  // main end (assumes the row's start reaches my_sigma at my_t)
+  return true;
+}
 
-#if PAREM_PHASE_STATS
-  const uint32_t clk2 = (uint32_t)clock64();
-#endif
+// 5.-9. Resolve the chunk: row starts from the chunk's start state, the aggregate, the
+// look-back for the exclusive prefix, the row records; false when a wait ran out.
+template <int LAYOUT, int ESIZE>
+__device__ __forceinline__ bool resolve_chunk(const ChunkCtx<LAYOUT, ESIZE>& C, const RowSpec& R,
+                                              const RowMain& M) {
+  const uint32_t lane = C.lane;
+  const DeviceDfa& D = C.p.dfa;
+  const uint32_t dead = C.dead;
+  const uint32_t A = C.A;
+  const uint64_t row0 = C.row0;
+  const uint64_t myrow = C.myrow;
+  const bool active = C.active;
+  const uint32_t nrows = C.nrows;
+  const uint8_t* const body = C.body;
+  const uint64_t rowlen = C.rowlen;
+  const Tab<LAYOUT, ESIZE>& tab = C.tab;
+  const ScanParams& p = C.p;
+  const uint64_t j = C.j;
+  auto cand_class = [&](uint64_t r) -> uint32_t { return C.cand_class(r); };
+  auto& my_t = R.my_t;
+  auto& my_sigma = R.my_sigma;
+  auto& my_conv = R.my_conv;
+  auto& head_cnt = R.head_cnt;
+  auto& mu = M.mu;
+  auto& fv = M.fv;
+  auto& fs = M.fs;
+  auto& lvv = M.lvv;
+  auto& ls = M.ls;
+  auto& lv = M.lv;
+  auto& nrec = M.nrec;
+  auto& E = M.E;
   // the match bitmap of row r (the merged prefix replays below write its bits [0, t))
   auto row_bits = [&](uint64_t r) -> uint16_t* {
     return p.match_bits != nullptr ? reinterpret_cast<uint16_t*>(p.match_bits) + (r * p.S) / 16 : nullptr;
@@ -1329,7 +1569,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
       }
     }
     w = __shfl_sync(kFull, w, 0);
-    if ((w >> 62) == 0) return;  // failed: the error word is set
+    if ((w >> 62) == 0) return false;  // failed: the error word is set
     s_j = (uint32_t)((w >> 45) & 0xFFFFu);
     if (s_j >= D.n) {  // never happens for a consistent status word; keep indices valid
       set_error(p.result, kErrInternal);
@@ -1489,7 +1729,7 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     }
     if (!ok) {
       set_error(p.result, kErrTimeout);
-      return;
+      return false;
     }
   }
   const Pfx inc = pfx_op(ex, agg);
@@ -1552,8 +1792,44 @@ __device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>
     p.result->count = inc.count;
     if (p.early != nullptr) write_early(p.early, inc.dead ? dead : E_chunk, inc.count, read_error(p.result));
   }
+  return true;
+}
+
+// One chunk of 32 rows (row k on lane k) by one warp: Algorithm 1 per row.  The rows'
+// candidate sets (the states entered on the byte that ends the previous row) are run until
+// they merge (steps 1-3); each lane then runs its merged state over the rest of its row
+// (step 4); the chunk's start state from chunk j - 1 fixes every row's true start, the merged
+// prefixes are counted, and the chunk publishes its aggregate and inclusive prefix for the
+// look-back of later chunks (steps 5-9).
+template <int LAYOUT, int ESIZE, int P>
+__device__ __forceinline__ void scan_chunk(WarpCtx& wc, const Tab<LAYOUT, ESIZE>& tab, const ScanParams& p,
+                                           const CUtensorMap* tmap, const uint64_t j) {
 #if PAREM_PHASE_STATS
-  if (lane == 0) {
+  const uint32_t clk0 = (uint32_t)clock64();
+#endif
+  ChunkCtx<LAYOUT, ESIZE> C(wc, tab, p, tmap, j);
+  RowSpec R;
+  chunk_begin(C, R);
+  find_sync_byte(C, R);
+  if constexpr (P == 1) {
+    speculate_grouped(C, R);
+  } else {
+    speculate_warp<LAYOUT, ESIZE, P>(C, R);
+    speculate_lanes<LAYOUT, ESIZE, P>(C, R);
+  }
+  record_convergence(C, R);
+  run_slot_maps(C, R);
+#if PAREM_PHASE_STATS
+  const uint32_t clk1 = (uint32_t)clock64();
+#endif
+  RowMain M;
+  if (!main_run(C, R, M)) return;
+#if PAREM_PHASE_STATS
+  const uint32_t clk2 = (uint32_t)clock64();
+#endif
+  if (!resolve_chunk(C, R, M)) return;
+#if PAREM_PHASE_STATS
+  if (C.lane == 0) {
     // 32-bit cycle differences (a chunk takes far less than 2^32 cycles)
     wc.cyc[0] += clk1 - clk0;
     wc.cyc[1] += clk2 - clk1;
