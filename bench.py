@@ -87,7 +87,7 @@ def profiled_traffic(config, n, plan):
         d = json.load(f)
     if d.get("kernel_hash") != kernel_hash():
         return None
-    if any(d.get(k) != plan.get(k) for k in ("warps_per_block", "blocks")):
+    if any(d.get(k) != plan.get(k) for k in ("warps_per_block", "blocks")) or not d.get("text_bytes"):
         return None
     return int(round(d["dram_bytes_per_launch"] * n / d["text_bytes"]))
 
@@ -348,13 +348,19 @@ def batch_measure(args, rank, world, dev, dist):
     n_texts = args.batch_texts
     specs = wl.batch_dfas(32, seed=6)
     lengths = wl.batch_lengths(n_texts, seed=6 + rank)
-    arena, offs = wl.batch_texts_device(specs, lengths, dev, seed=6 + rank)
     dfas = [pm.parem_load_dfa(s.table, s.byte_to_symbol, s.start, s.accept) for s in specs]
+    # the texts in the batch: all, or (--batch-dfa) those of one DFA alone, generated alone
+    keep = [i for i in range(n_texts) if args.batch_dfa < 0 or i % len(dfas) == args.batch_dfa]
+    if args.batch_dfa >= 0:
+        arena, offs = wl.batch_texts_device([specs[args.batch_dfa]], lengths[keep], dev, seed=6 + rank)
+    else:
+        arena, offs = wl.batch_texts_device(specs, lengths, dev, seed=6 + rank)
     ptr = arena.data_ptr()
-    items = [(dfas[i % len(dfas)], ptr + int(offs[i]), int(lengths[i]), None, 0) for i in range(n_texts)]
-    total = int(lengths.sum())
+    at = {i: int(offs[k if args.batch_dfa >= 0 else i]) for k, i in enumerate(keep)}  # text i's arena offset
+    items = [(dfas[i % len(dfas)], ptr + at[i], int(lengths[i]), None, 0) for i in keep]
+    total = int(sum(int(lengths[i]) for i in keep))
     t0 = time.perf_counter()
-    batch = pm.parem_batch_create(items, pm.BatchOpts(autotune=1))
+    batch = pm.parem_batch_create(items, pm.BatchOpts(autotune=0 if args.batch_no_autotune else 1))
     plan_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -386,7 +392,7 @@ def batch_measure(args, rank, world, dev, dist):
     # what the autotuner chose for each DFA (its longest rows; shorter texts get one row)
     per_dfa = []
     for d in range(len(dfas)):
-        mine = [c for i, c in enumerate(cfgs) if i % len(dfas) == d and c["segment_bytes"]]
+        mine = [c for k, c in enumerate(cfgs) if keep[k] % len(dfas) == d and c["segment_bytes"]]
         if not mine:
             continue
         info = pm.parem_dfa_get_info(dfas[d])
@@ -395,7 +401,7 @@ def batch_measure(args, rank, world, dev, dist):
                         "table": "smem" if mine[0]["smem_table"] else "l2"})
     tuned = {"warps_per_block": cfgs[0]["warps_per_block"], "per_dfa": per_dfa}
     # plain: one parem_match per text on the same stream (same texts)
-    for i in range(min(64, n_texts)):
+    for i in range(min(64, len(items))):
         pm.parem_match(items[i][0], items[i][1], length=items[i][2])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -408,8 +414,8 @@ def batch_measure(args, rank, world, dev, dist):
     if rank == 0:
         # the oracle on every text, all host cores; parity of every item
         host = arena.cpu().numpy()
-        jobs = [(specs[i % len(specs)], host[int(offs[i]):int(offs[i]) + int(lengths[i])], specs[i % len(specs)].start)
-                for i in range(n_texts)]
+        jobs = [(specs[i % len(specs)], host[at[i]:at[i] + int(lengths[i])], specs[i % len(specs)].start)
+                for i in keep]
         want, cpu_s, threads = oracle_all_cores(jobs)
         bad = [i for i, (g, w) in enumerate(zip(res, want))
                if (int(g.final_state), int(g.match_count)) != (int(w.final_state), int(w.match_count))]
@@ -422,20 +428,21 @@ def batch_measure(args, rank, world, dev, dist):
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": CONFIGS["d4"]["workload"], "texts": n_texts, "text_bytes": total, "dfas": len(dfas),
+            "config": {"workload": CONFIGS["d4"]["workload"], "texts": len(keep), "only_dfa": args.batch_dfa if args.batch_dfa >= 0 else None,
+                       "autotuned": not args.batch_no_autotune, "text_bytes": total, "dfas": len(dfas),
                        "positions": "count only", "plan_seconds_with_autotune": round(plan_s, 3),
                        "segment_bytes_median": int(np.median([x for x in segs if x] or [0])),
                        "l2": "inputs larger than L2 (7.27 GB)", "parallelism": f"replicas x{world}"},
             "p50_ms": round(step_ms[len(step_ms) // 2], 4),
             "p99_ms": round(step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))], 4),
             "batched_vs_plain": {"batched_gbs": round(value / world, 2), "plain_gbs": round(plain_gbs, 2),
-                                 "speedup": round(value / world / plain_gbs, 2), "plain_calls": n_texts,
+                                 "speedup": round(value / world / plain_gbs, 2), "plain_calls": len(keep),
                                  "results_agree": agree},
             "autotuned": tuned,
-            "parity": {"ok": not bad, "checked": f"all {n_texts} items: final state and match count vs the oracle",
+            "parity": {"ok": not bad, "checked": f"all {len(keep)} items: final state and match count vs the oracle",
                        "mismatched_items": bad[:8]},
             "cpu_baseline": {"value": round(total / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
-                             "sample": f"all {n_texts} texts ({total / 1e9:.2f} GB), independent oracle scans on "
+                             "sample": f"all {len(keep)} texts ({total / 1e9:.2f} GB), independent oracle scans on "
                                        f"{threads} host threads ({cpu_s:.1f} s)"},
             "roofline": {"bound": "hbm", "kernel": "whole batch graph (k_batch_scan + tiny kernel + copies)",
                          "achieved": round(achieved, 1), "peak": peak,
@@ -885,7 +892,7 @@ def summarize_ncu(args):
         def num(m):
             scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(units[col[m]], 1)
             return float(v[col[m]].replace(",", "")) * scale
-        d = {"kernel_hash": kernel_hash(), "config": args.config, "text_bytes": args.size_mb << 20,
+        d = {"kernel_hash": kernel_hash(), "config": args.config, "text_bytes": (args.size_mb << 20) if args.size_mb else CONFIGS[args.config]["n"],
              "segment_bytes": args.segment_bytes, "warps_per_block": int(num("launch__block_size")) // 32,
              "blocks": int(num("launch__grid_size")),
              "dram_bytes_per_launch": int(num("dram__bytes_read.sum") + num("dram__bytes_write.sum")),
@@ -946,6 +953,10 @@ def main():
     ap.add_argument("--segment-bytes", type=int, default=0,
                     help="fix the row length (profiling captures of a smaller text with the full-size plan)")
     ap.add_argument("--batch-texts", type=int, default=4096, help="texts of the batched configuration")
+    ap.add_argument("--batch-dfa", type=int, default=-1,
+                    help="batched configuration: only the texts of this DFA (0-31), alone in the batch")
+    ap.add_argument("--batch-no-autotune", action="store_true",
+                    help="batched configuration: the planner's default plan instead of the autotuner's")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
     ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
     ap.add_argument("--arenas", type=int, default=32, help="batches in flight in the serving configuration")

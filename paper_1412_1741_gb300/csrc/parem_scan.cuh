@@ -1226,6 +1226,8 @@ __device__ __forceinline__ void run_slot_maps(const ChunkCtx<LAYOUT, ESIZE>& C, 
 // wait ran out.
 template <int LAYOUT, int ESIZE>
 __device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R, RowMain& M) {
+  // the match bitmap (dense emission) is never planned for the stride layouts: no code for it
+  constexpr bool kBits = LAYOUT != kByteStride && LAYOUT != kClassPair;
   uint8_t* const sm = C.wc.sm;
   const uint32_t lane = C.lane;
   const uint32_t stage0 = C.wc.stage0;
@@ -1382,7 +1384,7 @@ __device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R,
                 mu += (x >= A);
               }
             }
-          } else if (p.match_bits != nullptr) {
+          } else if (kBits && p.match_bits != nullptr) {
             // dense matches: the accepting steps of the vector as a 16-bit mask for the match
             // bitmap (stored once per block below)
             uint32_t mb = 0;
@@ -1423,7 +1425,7 @@ __device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R,
           }
         }
       }
-      if (p.match_bits != nullptr) {
+      if (kBits && p.match_bits != nullptr) {
         // bits [myrow * S + col0, + BOX) of the body: BOX-bit aligned (S and col0 are)
         const uint64_t bit0 = myrow * p.S + col0;
         if constexpr (BOX == 64) {
@@ -1478,7 +1480,7 @@ __device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R,
         }
       }
       // bits [R * S + o, + 16) of the body (16-bit aligned)
-      if (p.match_bits != nullptr)
+      if (kBits && p.match_bits != nullptr)
         reinterpret_cast<uint16_t*>(p.match_bits)[(p.R * p.S + o) / 16] = (uint16_t)tbits;
     }
   }
@@ -1491,6 +1493,8 @@ __device__ __forceinline__ bool main_run(ChunkCtx<LAYOUT, ESIZE>& C, RowSpec& R,
 template <int LAYOUT, int ESIZE>
 __device__ __forceinline__ bool resolve_chunk(const ChunkCtx<LAYOUT, ESIZE>& C, const RowSpec& R,
                                               const RowMain& M) {
+  // the match bitmap (dense emission) is never planned for the stride layouts: no code for it
+  constexpr bool kBits = LAYOUT != kByteStride && LAYOUT != kClassPair;
   const uint32_t lane = C.lane;
   const DeviceDfa& D = C.p.dfa;
   const uint32_t dead = C.dead;
@@ -1519,7 +1523,7 @@ __device__ __forceinline__ bool resolve_chunk(const ChunkCtx<LAYOUT, ESIZE>& C, 
   auto& E = M.E;
   // the match bitmap of row r (the merged prefix replays below write its bits [0, t))
   auto row_bits = [&](uint64_t r) -> uint16_t* {
-    return p.match_bits != nullptr ? reinterpret_cast<uint16_t*>(p.match_bits) + (r * p.S) / 16 : nullptr;
+    return kBits && p.match_bits != nullptr ? reinterpret_cast<uint16_t*>(p.match_bits) + (r * p.S) / 16 : nullptr;
   };
   // 5. the chunk's end state is known now if every row merged
   //    (or if at least its last row did: E_last does not depend on the chunk's start, and
@@ -1782,7 +1786,7 @@ __device__ __forceinline__ bool resolve_chunk(const ChunkCtx<LAYOUT, ESIZE>& C, 
         // or every match of the row is in the match bitmap: the prefix [0, t) replayed from the
         // row's true start wrote its bits, the main run the rest (a run that died inside the
         // prefix is replayed by the emit pass instead)
-        if (!died_pre && p.match_bits != nullptr) sr.flags |= kBitsFlag;
+        if (!died_pre && kBits && p.match_bits != nullptr) sr.flags |= kBitsFlag;
       }
       p.segrec[myrow] = sr;
     }
