@@ -494,15 +494,35 @@ int create_internal(const parem_batch_item* items, uint32_t n, const parem_batch
     wsum += slots[si].weight;
   }
   {
-    std::vector<std::pair<double, uint32_t>> rem;
-    int given = 0;
+    // Slots whose chunks are long serial chains (candidate sets beyond the registers, merged
+    // through the state bitmap) first get enough blocks to start all their chunks at once:
+    // otherwise their last chunks start when the first ones end, and the batch waits on two
+    // chunk lengths.  The rest of the grid goes by weight.
     std::vector<int> quota(ns, 0);
+    int floor_sum = 0;
+    for (uint32_t si = 0; si < ns; ++si) {
+      if (slots[si].spec == PAREM_BATCH_SPEC_WARP_BITMAP && slots[si].dfa->host.max_cand > 8 * kLanes) {
+        quota[si] = (int)((slot_chunks[si] + warps - 1) / warps);
+        floor_sum += quota[si];
+      }
+    }
+    if (floor_sum > b->grid) {
+      const int want = floor_sum;
+      floor_sum = 0;
+      for (uint32_t si = 0; si < ns; ++si) {
+        quota[si] = (int)((int64_t)quota[si] * b->grid / want);
+        floor_sum += quota[si];
+      }
+    }
+    const int rest = b->grid - floor_sum;
+    std::vector<std::pair<double, uint32_t>> rem;
+    int given = floor_sum;
     for (uint32_t si = 0; si < ns; ++si) {
       if (slots[si].weight <= 0) continue;
-      const double q = wsum > 0 ? slots[si].weight / wsum * b->grid : 0;
-      quota[si] = (int)std::floor(q);
-      given += quota[si];
-      rem.push_back({q - quota[si], si});
+      const double q = wsum > 0 ? slots[si].weight / wsum * rest : 0;
+      quota[si] += (int)std::floor(q);
+      given += (int)std::floor(q);
+      rem.push_back({q - std::floor(q), si});
     }
     std::sort(rem.begin(), rem.end(), [](auto& a, auto& c) { return a.first > c.first; });
     for (size_t r = 0; given < b->grid && r < rem.size(); ++r, ++given) quota[rem[r].second]++;
