@@ -490,7 +490,7 @@ def serve_measure(args, rank, world, dev):
                 "p50_run_ms": round(float(np.percentile(run, 50)), 3),
                 "errors": int((resp["status"] != 0).sum())}
 
-    srv = pm.parem_server_create(dfas, pm.ServerOpts(arenas=args.arenas))
+    srv = pm.parem_server_create(dfas, pm.ServerOpts(arenas=args.arenas, arena_scratch_bytes=args.arena_mb << 20))
     for w in range(args.warmup):
         srv.replay(trace(20000, 0.2, 100 + w))
     k0 = srv.stats()["kernels"]
@@ -553,7 +553,7 @@ def serve_measure(args, rank, world, dev):
                        "step": "one replay of the whole trace"},
             "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
             "serving": {"batched": main, "batches": st["batches"], "max_batch": st["max_batch"],
-                        "arenas": args.arenas,
+                        "arenas": args.arenas, "arena_scratch_mib": args.arena_mb or None,
                         "fifo_plain": dict(fsum, trace_seconds=args.fifo_seconds), "fifo_results_agree": agree,
                         "saturation_sweep": sweep, "max_sustained_gbs": best["gbs"]},
             "parity": {"ok": not bad, "checked": f"the first {len(jobs)} requests of the trace ({nb / 1e9:.1f} GB): "
@@ -962,7 +962,8 @@ def main():
                     help="batched configuration: the planner's default plan instead of the autotuner's")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="trace length of the serving configuration")
     ap.add_argument("--fifo-seconds", type=float, default=0.25, help="trace head replayed through the FIFO server")
-    ap.add_argument("--arenas", type=int, default=32, help="batches in flight in the serving configuration")
+    ap.add_argument("--arenas", type=int, default=256, help="batches in flight in the serving configuration")
+    ap.add_argument("--arena-mb", type=int, default=0, help="device scratch per server arena in MiB (0: the library's)")
     ap.add_argument("--serve-oracle-gb", type=float, default=20.0,
                     help="bytes of the serving trace's first requests the oracle checks (GB)")
     ap.add_argument("--enumerate", action="store_true",

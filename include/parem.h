@@ -443,13 +443,13 @@ typedef struct parem_server parem_server;
 
 typedef struct {
   uint32_t mode;                 /* PAREM_SERVE_BATCH (default) or PAREM_SERVE_FIFO */
-  uint32_t arenas;               /* batches in flight (0 = 32): a batch that holds a long request
+  uint32_t arenas;               /* batches in flight (0 = 256): a batch that holds a long request
                                     keeps its arena until that request is done, so many
                                     arenas keep the GPU busy behind it */
   uint32_t max_items;            /* requests per batch (0 = 4096) */
   uint32_t reserved0;
   uint64_t max_batch_bytes;      /* text bytes per batch (0 = 1 GiB) */
-  uint64_t arena_scratch_bytes;  /* device scratch per arena (0 = 256 MiB) */
+  uint64_t arena_scratch_bytes;  /* device scratch per arena (0 = 128 MiB) */
   uint64_t reserved[4];
 } parem_server_opts;
 

@@ -14,8 +14,9 @@
 //   fit is halved and the rest goes back to the head of the queue).
 // * With several arenas the next batches are launched while earlier ones run: their thread
 //   blocks start as soon as blocks of the running batches retire, so new arrivals do not
-//   wait for the slowest request of a batch ahead of them (32 arenas by default: with 2, a
-//   long request held the GPU's throughput to a third of that).
+//   wait for the slowest request of a batch ahead of them (256 arenas by default: with 2, a
+//   long request held the GPU's throughput to a third of the offered load, and with 32 the
+//   arenas held by long requests made new arrivals queue for half of their p50 latency).
 // * FIFO mode serves one request at a time with parem_match (the plain comparison).
 #include <cuda_runtime.h>
 
@@ -399,9 +400,9 @@ extern "C" int parem_server_create(parem_dfa* const* dfas, uint32_t n_dfas, cons
         return rc;
       }
     }
-    const uint32_t n_arenas = s->opts.arenas ? s->opts.arenas : 32;
+    const uint32_t n_arenas = s->opts.arenas ? s->opts.arenas : 256;
     const uint32_t max_items = s->opts.max_items ? s->opts.max_items : 4096;
-    const uint64_t scratch = s->opts.arena_scratch_bytes ? s->opts.arena_scratch_bytes : (256ull << 20);
+    const uint64_t scratch = s->opts.arena_scratch_bytes ? s->opts.arena_scratch_bytes : (128ull << 20);
     // descriptors: per item its scan parameters and tensor map, per slot its record, the CTA
     // assignment and the emit block lists
     const uint64_t desc = (uint64_t)max_items * (sizeof(BatchItem) + 64) + (scratch / 64) + (1u << 20);
