@@ -767,6 +767,14 @@ def scan_line(args, rank, world, dev, dist):
             re2e = pm.parem_match_host(dfa, host_text, host_pos)
             step_s.append(time.perf_counter() - t0)
         link = host_link_gbs(host_text, text) if n >= (64 << 20) else None
+        # the same number of plain pinned host-to-device copies of the text, each timed alone:
+        # what the host path would take if scanning were free (its slow steps are the link's)
+        copy_s = []
+        for _ in range(e2e_steps):
+            t0 = time.perf_counter()
+            text.copy_(host_text, non_blocking=True)
+            torch.cuda.synchronize()
+            copy_s.append(time.perf_counter() - t0)
         if rank == 0:
             # the mean over the steps is the headline; the median and the measured host link
             # (pinned host-to-device copy of the same buffer) are reported beside it
@@ -775,7 +783,9 @@ def scan_line(args, rank, world, dev, dist):
                            "steps": e2e_steps, "statistic": "mean over steps",
                            "median_value": round(n / sorted(step_s)[len(step_s) // 2] / 1e9, 2),
                            "step_ms": [round(x * 1e3, 2) for x in step_s],
-                           "host_link_gbs": round(link, 2) if link else None}
+                           "host_link_gbs": round(link, 2) if link else None,
+                           "plain_copy_mean_gbs": round(n * e2e_steps / sum(copy_s) / 1e9, 2),
+                           "plain_copy_step_ms": [round(x * 1e3, 2) for x in copy_s]}
         del host_text, host_pos
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"], line["parity"] = cpu_baseline_and_parity(spec, text, r, pos)
