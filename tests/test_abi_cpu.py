@@ -113,3 +113,44 @@ def test_null_pointers_are_rejected(lib):
     assert lib.parem_load_dfa(None, 1, 1, None, 0, None, ctypes.byref(res)) == -1
     assert lib.parem_match(None, None, 0, None, 0, None, None) == -1
     assert lib.parem_dfa_get_info(None, None) == -1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding marshals has the C layout of include/parem.h: a C program
+    compiled against the header prints each struct's size and each field's offset, which must
+    equal the ctypes mirrors' (and the numpy records' for requests and responses)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = [("parem_result", pm._Result), ("parem_dfa_info", pm._Info), ("parem_match_opts", pm.MatchOpts),
+               ("parem_stats", pm.Stats), ("parem_pair_info", pm._PairInfo), ("parem_batch_item", pm._BatchItem),
+               ("parem_batch_opts", pm.BatchOpts), ("parem_batch_config", pm._BatchConfig),
+               ("parem_server_opts", pm.ServerOpts), ("parem_server_stats", pm._ServerStats)]
+    records = [("parem_request", pm.REQUEST_DTYPE), ("parem_response", pm.RESPONSE_DTYPE)]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "parem.h"', "int main(void) {"]
+    want = {}
+    for cname, cls in mirrors:
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        want[cname] = ctypes.sizeof(cls)
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+            want[f"{cname}.{fname}"] = getattr(cls, fname).offset
+    nested = {"final_state", "accepted", "match_count", "n_written"}  # the response's parem_result
+    for cname, dt in records:
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        want[cname] = dt.itemsize
+        for fname in dt.names:
+            member = f"result.{fname}" if cname == "parem_response" and fname in nested else fname
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {member}));')
+            want[f"{cname}.{fname}"] = dt.fields[fname][1]
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.rsplit(" ", 1) for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                           check=True).stdout.splitlines())
+    assert {k: int(v) for k, v in got.items()} == want
