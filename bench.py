@@ -64,6 +64,24 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+
+        model = platform.processor() or platform.machine()
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -231,7 +249,8 @@ def run_reference(args, rank):
         "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": CONFIGS[args.config]["workload"], "sample_bytes": sample, "matches_in_sample": r.match_count},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
+                         "host": host_cpu()},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -266,7 +285,7 @@ def cpu_baseline_and_parity(spec, text_dev, got, pos_dev):
     parity = {"ok": ok, "checked": "whole text" + (", every position" if pos_dev is not None else ", count only"),
               "text_bytes": n, "oracle_matches": int(want.match_count), "gpu_matches": int(got.match_count),
               "oracle_final_state": int(want.final_state), "gpu_final_state": int(got.final_state), **checks}
-    cpu = {"value": round(n / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+    cpu = {"value": round(n / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
            "sample": f"the whole {n / (1 << 30):.2f} GiB text, one single-threaded pass of the C oracle writing "
                      f"its {want.match_count} positions ({dt:.1f} s; a counting pass before it sizes the buffer)"}
     return cpu, parity
@@ -442,6 +461,7 @@ def batch_measure(args, rank, world, dev, dist):
             "parity": {"ok": not bad, "checked": f"all {len(keep)} items: final state and match count vs the oracle",
                        "mismatched_items": bad[:8]},
             "cpu_baseline": {"value": round(total / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"all {len(keep)} texts ({total / 1e9:.2f} GB), independent oracle scans on "
                                        f"{threads} host threads ({cpu_s:.1f} s)"},
             "roofline": {"bound": "hbm", "kernel": "whole batch graph (k_batch_scan + tiny kernel + copies)",
@@ -560,6 +580,7 @@ def serve_measure(args, rank, world, dev):
                                                  f"final state, match count and status vs the oracle",
                        "mismatched_requests": bad[:8]},
             "cpu_baseline": {"value": round(nb / cpu_s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"the first {len(jobs)} requests of the trace ({nb / 1e9:.1f} GB), independent "
                                        f"oracle scans on {threads} host threads ({cpu_s:.1f} s)"},
             "e2e": {"value": main["gbs"], "unit": "GB/s", "h2d_bytes_per_step": int(len(req)) * 56,
