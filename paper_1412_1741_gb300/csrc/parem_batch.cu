@@ -721,10 +721,11 @@ extern "C" int parem_batch_create(const parem_batch_item* items, uint32_t n_item
         }
       };
       for (double g : {0.25, 0.5, 2.0, 4.0}) trial(clamp_s((double)s0 * g), f0);
-      // the other forms that apply to this DFA, around the best size so far
+      // the other forms that apply to this DFA, around the best size so far (unless the caller
+      // fixed the form)
       const uint64_t s1 = pick_s;
       for (uint32_t f : {PAREM_BATCH_SPEC_GROUPED, PAREM_BATCH_SPEC_WARP, PAREM_BATCH_SPEC_WARP_BITMAP}) {
-        if (f == f0 || resolve_spec(d, f) != f) continue;
+        if (o.spec != PAREM_BATCH_SPEC_AUTO || f == f0 || resolve_spec(d, f) != f) continue;
         for (double g : {1.0, 0.5, 2.0}) trial(clamp_s((double)s1 * g), f);
       }
       best_of[d] = {pick_s, pick_f};

@@ -162,3 +162,16 @@ def test_batch_autotuner_reports_one_form_per_dfa(torch):
         if c["segment_bytes"]:
             assert form_of.setdefault(id(dfa), c["spec"]) == c["spec"]
     batch.free()
+
+
+def test_batch_autotuner_keeps_a_form_the_caller_fixed(torch):
+    """With the form fixed by the caller, the autotuner only tunes row lengths and the block
+    shape: every DFA where the form applies keeps it, and results equal the per-item scans."""
+    dfas, texts, items, want = _make(torch, n_items=24, seed=13, max_len=4 << 20)
+    batch = pm.parem_batch_create(items, pm.BatchOpts(autotune=1, spec=pm.PAREM_BATCH_SPEC_WARP_BITMAP))
+    batch.run()
+    _check(batch, items, want)
+    for (dfa, _, _), c in zip(items, batch.configs()):
+        if c["segment_bytes"] and _expected_form(pm.parem_dfa_get_info(dfa), pm.PAREM_BATCH_SPEC_WARP_BITMAP):
+            assert c["spec"] == "warp_bitmap"
+    batch.free()
