@@ -906,7 +906,16 @@ uint32_t batch_order(const parem_batch* b, uint32_t k) { return b->order[k]; }
 int batch_prepare_dfa(parem_dfa* d) { return ensure_batch_dfa(d); }
 
 uint64_t batch_default_segment(const parem_dfa* d) {
-  return std::min(std::max<uint64_t>(4096, min_row_bytes(d, 8)), max_row_bytes(d, d->host.max_cand));
+  // latency first: a request is answered when its slowest chunk is, and a chunk's main run is
+  // one dependent lookup per byte of its rows, so rows are a few synchronisation lengths long
+  // (4 x the estimate, 1.25 x the longest merge seen) rather than the planner's 16 x, which
+  // pays for throughput with rows of up to several hundred KiB on many-state DFAs
+  const Prepared& H = d->host;
+  const uint64_t est = H.sync_len == kNoSync ? 0 : H.sync_len;
+  const uint64_t conv = d->conv_hint.load();
+  uint64_t S = std::max<uint64_t>(4096, std::max<uint64_t>(4 * est, conv + conv / 4));
+  S = (S + kBox - 1) / kBox * kBox;
+  return std::min(std::min(S, std::max<uint64_t>(4096, min_row_bytes(d, 8))), max_row_bytes(d, H.max_cand));
 }
 
 }  // namespace parem
