@@ -27,3 +27,38 @@ def test_reference_arm_prints_one_contract_line(config):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_profiled_traffic_scales_and_refuses_what_does_not_match(tmp_path, monkeypatch):
+    """roofline.traffic: the committed capture's DRAM bytes scaled to the run's text size, or
+    None when the kernel sources, the launch shape or the capture's text size do not fit."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    plan = {"warps_per_block": 24, "blocks": 152}
+
+    def write(**kw):
+        d = {"kernel_hash": "h", "config": "dx", "text_bytes": 1 << 30, "warps_per_block": 24, "blocks": 152,
+             "dram_bytes_per_launch": 3 << 29}
+        d.update(kw)
+        (tmp_path / "profiles" / "traffic_dx.json").write_text(json.dumps(d))
+
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "h")
+    write()
+    assert bench.profiled_traffic("dx", 4 << 30, plan) == 6 << 30  # 1.5 B per text byte, 4 GiB
+    assert bench.profiled_traffic("dx", 4 << 30, dict(plan, warps_per_block=23)) is None
+    write(kernel_hash="other")
+    assert bench.profiled_traffic("dx", 4 << 30, plan) is None
+    write(kernel_hash="h", text_bytes=0)
+    assert bench.profiled_traffic("dx", 4 << 30, plan) is None
+    assert bench.profiled_traffic("none", 4 << 30, plan) is None
+
+
+def test_host_cpu_names_a_model_and_the_core_count():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.host_cpu()
+    assert isinstance(h["model"], str) and h["model"] and h["nproc"] == os.cpu_count()
