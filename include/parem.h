@@ -371,7 +371,8 @@ typedef struct {
   uint32_t autotune;        /* 1: choose each DFA's segment size and speculation form by timing
                                candidates on its own items, and the block shape by timing the
                                whole batch (several trial runs during parem_batch_create) */
-  uint32_t warps_per_block; /* 0 = 24; 1..16 = 16 warps (128 registers each); > 16 = 24 (80) */
+  uint32_t warps_per_block; /* 0 = 24, or with autotune the faster of 24 and 16; 1..16 = 16 warps
+                               (128 registers each); > 16 = 24 (80 registers each) */
   uint64_t segment_bytes;   /* 0 = planner/autotuner; else the same S for every item */
   uint32_t use_graph;       /* 0: launch the kernels directly in parem_batch_run; else (default
                                when the struct is NULL) replay the captured CUDA graph */
