@@ -11,8 +11,9 @@
 //   * texts shorter than one 64-byte row go to a one-thread-per-item kernel;
 //   * one scratch allocation holds every item's status words, row records, recorded positions,
 //     slot maps and result word; one descriptor allocation holds the per-item scan parameters
-//     and TMA tensor maps, the slots, and the initial CTA -> slot assignment (in proportion to
-//     each slot's bytes, weighted up when its table is read from L2);
+//     and TMA tensor maps, the slots, and the initial CTA -> slot assignment (first enough CTAs
+//     for the slots of long serial chunks to start all of them at once, then the rest in
+//     proportion to each slot's bytes, weighted up when its table is read from L2);
 //   * clearing the scratch, the kernels and the copy of the results to pinned host memory are
 //     captured in one CUDA graph, which parem_batch_run replays.
 #include <cuda.h>
